@@ -1,0 +1,67 @@
+"""The oracle's pins must be able to fail.
+
+Each case plants one plausible mistake (a flipped sign, a dropped term, a
+shifted stagger, a wrong face) in a temporary copy of the oracle source, on
+the CPU, and checks that the pin named beside it now fails.  Nothing here
+touches a GPU.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("boris rotation sign", "vm[1] * b[2] - vm[2] * b[1]", "vm[2] * b[1] - vm[1] * b[2]",
+     "test_boris_pure_B_conserves_speed_and_rotates_2atan_b or test_boris_ExB_drift_direction"),
+    ("Esirkepov dropped 1/2 term",
+     "0.5 * S0[1][j] * DS[2][k] + DS[1][j] * DS[2][k] / 3.0);\n                    run += W;\n"
+     "                    if (run != 0.0) fadd(s, s->J[0]",
+     "0.0 * S0[1][j] * DS[2][k] + DS[1][j] * DS[2][k] / 3.0);\n                    run += W;\n"
+     "                    if (run != 0.0) fadd(s, s->J[0]",
+     "test_esirkepov_satisfies_continuity_exactly"),
+    ("E_x stagger", "{{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}}",
+     "{{0.0, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}}", "test_gather_is_exact_for_linear_fields"),
+    ("Yee curl sign", "s->B[2][c] -= dt * (tBzx - tBzy);", "s->B[2][c] -= dt * (tBzx + tBzy);",
+     "test_yee_plane_waves_follow_numerical_dispersion"),
+    ("Hooke force sign",
+     "kick[a] = 0.5 * dt * (q / m * E[a] - omega0[a] * omega0[a] * D[a]);",
+     "kick[a] = 0.5 * dt * (q / m * E[a] + omega0[a] * omega0[a] * D[a]);",
+     "test_bound_push_reproduces_taflove_recurrence"),
+    ("damping sign", "rhs[r] = (1.0 - 0.5 * dt * gamma[r]) * vm[r];",
+     "rhs[r] = (1.0 + 0.5 * dt * gamma[r]) * vm[r];", "test_bound_damping_factor"),
+    ("reflection not mirrored", "X1[a] = 2.0 * face - X1[a];", "X1[a] = X0[a];",
+     "test_reflection_hand_computed"),
+    ("source sign", "double Js = -2.0 * s->E0", "double Js = 2.0 * s->E0",
+     "test_soft_source_launches_E0_pulse"),
+    ("CPML coefficient sign", "*c = *b - 1.0;", "*c = 1.0 - *b;", "test_cpml_absorbs_the_pulse"),
+    ("FD density of states", "return (L->dirac ? p : p * p) * f;",
+     "return (L->dirac ? p : p * p * p) * f;", "test_fd_finite_temperature_sommerfeld_3d"),
+    ("2D3V J_z factor", "double fz = qw * vz / (d[0] * d[1] * d[2]);",
+     "double fz = 0.5 * qw * vz / (d[0] * d[1] * d[2]);",
+     "test_esirkepov_satisfies_continuity_exactly"),
+    ("Dirac renormalisation", "v[0] = vF * v[0] / nrm;", "v[0] = vF * v[0] / (nrm * 1.0000001);",
+     "test_dirac_speed_is_vF"),
+    ("Philox key increment", "k0 += 0x9E3779B9u;", "k0 += 0x9E3779B7u;",
+     "test_philox_known_answers"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, pin):
+    src = open(os.path.join(ROOT, "oracle", "pic_oracle.c")).read()
+    assert old in src, f"mutation site for '{name}' not found"
+    (tmp_path / "oracle").mkdir()
+    (tmp_path / "oracle" / "pic_oracle.c").write_text(src.replace(old, new, 1))
+    shutil.copy(os.path.join(ROOT, "oracle", "oracle.py"), tmp_path / "oracle" / "oracle.py")
+    (tmp_path / "oracle" / "__init__.py").write_text("")
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
+    for f in ("test_oracle_pins.py", "conftest.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py", "-k", pin], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and "failed" in r.stdout, (name, r.stdout[-2000:])
