@@ -1,0 +1,236 @@
+/*
+ * pic.h -- C ABI of the GB300-native particle-in-cell step for quantum
+ * plasmas (Ngirmang, Do, Liu, Bosman & Wu, "Particle-In-Cell Simulations of
+ * Quantum Plasmas", arXiv 2501.07465).
+ *
+ * One simulation = a Yee grid (E on integer steps, B on half steps, Sec. 4.1),
+ * an optional material mask (Sec. 3) and up to PIC_MAX_SPECIES particle
+ * species of three kinds:
+ *   PIC_FREE  -- free carriers, Boris push (Appendix A.1, Eq. borisscheme),
+ *                optionally loaded from a Fermi-Dirac law (Sec. 2, Eq. fddist);
+ *   PIC_BOUND -- bound electrons on a damped harmonic tether (Sec. 4, Eq.
+ *                modlorentz), modified Boris push (Appendix A.2);
+ *   PIC_DIRAC -- massless Dirac carriers of a sheet in the x-y plane (Sec. 5):
+ *                Boris push with the transverse mass, |v| renormalised to v_F.
+ * A step gathers E^n and B^n to every particle (CIC), pushes it, reflects
+ * free and Dirac particles specularly at the material edges, deposits the
+ * current with Esirkepov's charge-conserving scheme and advances the fields
+ * with Yee FDTD (CPML layers and a soft plane-wave current sheet optional).
+ *
+ * Conventions for every call:
+ *  - Units are SI.  Cells are indexed x fastest: c = (k*ny + j)*nx + i.
+ *  - Host pointers are owned by the caller and only read or written during
+ *    the call.  Device state is owned by the simulation handle and freed by
+ *    pic_destroy.
+ *  - Calls never throw and never abort; they return a pic_status.  Work is
+ *    enqueued on the simulation's stream; errors found on the device (a
+ *    particle outside the domain, a wait that timed out) are latched and
+ *    returned by the next pic_sync, pic_diagnostics, pic_read_* call.
+ *  - A handle is not thread-safe: one host thread per handle at a time.
+ *  - Precision: fields, velocities and in-cell offsets are FP32; cell indices
+ *    int32; bound-particle anchors FP64; the loader's CDF inversion and the
+ *    diagnostics reductions FP64.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_MAX_SPECIES 8
+
+typedef enum pic_status {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,    /* bad argument (size, kind, layout) */
+    PIC_ENOMEM = 2,    /* device allocation failed */
+    PIC_EDTLIMIT = 3,  /* dt violates the stability limit of Eq. dtlimit */
+    PIC_ECUDA = 4,     /* a CUDA call failed; see pic_last_error */
+    PIC_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    PIC_ESTATE = 6,    /* call not valid in the handle's state */
+    PIC_EBOUNDS = 7,   /* a device-side bounds check fired */
+    PIC_EBUDGET = 8    /* a group's HBM budget would be exceeded */
+} pic_status;
+
+enum { PIC_BC_PERIODIC = 0, PIC_BC_PML = 1 };
+enum { PIC_FREE = 0, PIC_BOUND = 1, PIC_DIRAC = 2 };
+/* Fixed neutralising ions, used only by the Gauss-law diagnostic (ions carry
+   no current): none, at the loaded positions (anchors for bound species), or
+   uniform over the domain. */
+enum { PIC_BG_NONE = 0, PIC_BG_AT_PARTICLES = 1, PIC_BG_UNIFORM = 2 };
+/* bits of the `which` argument of pic_read_fields / pic_write_fields */
+enum {
+    PIC_EX = 1 << 0, PIC_EY = 1 << 1, PIC_EZ = 1 << 2,
+    PIC_BX = 1 << 3, PIC_BY = 1 << 4, PIC_BZ = 1 << 5,
+    PIC_JX = 1 << 6, PIC_JY = 1 << 7, PIC_JZ = 1 << 8
+};
+
+typedef struct pic_sim pic_sim;     /* opaque, owned by the library */
+typedef struct pic_group pic_group; /* opaque batch of simulations */
+
+/* Grid, time step and boundaries (Sec. 4.1).  2D runs are 2D3V in the x-y
+   plane (nz must be 1; dz is the slab depth used for densities).  Limits:
+   nx, ny <= 2048, nz <= 1024. */
+typedef struct pic_grid_desc {
+    int dims;           /* 2 or 3 */
+    int nx, ny, nz;     /* cells */
+    double dx, dy, dz;  /* cell size, m */
+    double dt;          /* time step, s; checked against Eq. dtlimit */
+    int bc[3];          /* PIC_BC_PERIODIC or PIC_BC_PML per axis (z ignored in 2D) */
+    int pml_cells;      /* CPML thickness on PML axes (cells) */
+    double pml_R0;      /* CPML target reflection; <= 0 selects 1e-8 */
+    int pml_order;      /* CPML grading exponent; <= 0 selects 3 */
+    /* Soft plane-wave drive: a one-cell current sheet normal to inc_axis at
+       index src_index carrying J_pol = -2 E0 g(t) / (eta0 d_inc), which
+       radiates E_pol = E0 g(t - |x - x_s|/c) to both sides, with
+       g(t) = exp(-2 ln2 (t - t0)^2 / tau^2) sin(omega (t - t0)). */
+    int src_on;
+    int inc_axis, pol_axis, src_index;
+    double E0, omega, tau, t0;
+} pic_grid_desc;
+
+/* One species.  q, m in C and kg; weight = physical particles per
+   macro-particle (ignored by the Fermi-Dirac loader, which sets it to
+   density * cell volume / ppc).  omega0 / gamma: binding frequency and
+   damping of PIC_BOUND (Eq. modlorentz; gamma must be isotropic: the three
+   entries equal).  v_F: Fermi velocity of PIC_DIRAC (m is then the averaged
+   transverse mass p_F / (2 v_F) of Sec. 5).  background: PIC_BG_*. */
+typedef struct pic_species_desc {
+    int kind;
+    double q, m, weight;
+    double omega0[3], gamma[3];
+    double v_F;
+    int background;
+} pic_species_desc;
+
+/* Particles of one species, either given explicitly (cell != NULL) or drawn
+   by the Fermi-Dirac loader (cell == NULL).
+   Explicit: n particles; cell[n] linear cell index; off[3n] in-cell offset in
+   [0,1) (x,y,z interleaved; free and Dirac); v[3n] velocity at t = -dt/2 (m/s);
+   for PIC_BOUND anchor_off[3n] (FP64, [0,1)) is the rest position inside
+   `cell` and disp[3n] (may be NULL = 0) the displacement from it in metres.
+   Loader (Sec. 2): every material cell (mask != 0, all cells without a
+   mask) gets ppc particles, particle id = material-cell rank * ppc + j;
+   Philox-4x32-10 with key = seed and counter (id_lo, id_hi, call, stream)
+   gives six uniforms per particle (position, |p|, direction); positions are
+   uniform in the cell, or the j-th point of an m^dims lattice when quiet
+   (m^dims = ppc); |p| follows the FD law with mu = E_F up to mu + 40 kT
+   (3D density p^2 f for free, 2D p f for Dirac); bound particles start at
+   rest.  density (m^-3) also feeds the plasma term of the dt check. */
+typedef struct pic_particles {
+    int64_t n;
+    const int32_t *cell;
+    const float *off;
+    const float *v;
+    const double *anchor_off;
+    const float *disp;
+    double density;
+    double E_F;   /* J */
+    double T;     /* K */
+    int ppc;
+    int quiet;
+    uint64_t seed;
+    uint32_t stream;
+} pic_particles;
+
+/* Tuning of one simulation (defaults in brackets; 0 keeps the default). */
+typedef struct pic_tuning {
+    int tile[3];        /* particle tile, cells [8,8,8 in 3D; 32,32,1 in 2D] */
+    int sort_interval;  /* steps between tile re-sorts [32] */
+    int field_zchunk;   /* z planes per field-kernel CTA [16] */
+    int particle_ctas;  /* persistent particle CTAs [SMs x occupancy] */
+    int keep_J;         /* 1: J of the last step stays readable (tests) [0] */
+    int timing;         /* 1: time every kernel launch with CUDA events [0] */
+} pic_tuning;
+
+/* Results of pic_diagnostics (FP64 reductions on the device). */
+typedef struct pic_diag {
+    int64_t step;                            /* steps taken */
+    double time;                             /* step * dt, s */
+    int nspecies;
+    int64_t count[PIC_MAX_SPECIES];          /* particles per species */
+    uint64_t reflections[PIC_MAX_SPECIES];   /* specular reflections so far */
+    double kinetic[PIC_MAX_SPECIES];         /* sum 1/2 m w |v|^2, J */
+    double field_E;                          /* sum eps0 E^2 / 2 dV, J */
+    double field_B;                          /* sum B^2 / (2 mu0) dV, J (B on the half step) */
+    double gauss_max;                        /* max |div E - rho/eps0| over nodes */
+    double gauss_rms;                        /* RMS of the same */
+    double rho_max;                          /* max |rho / eps0| */
+} pic_diag;
+
+/* Kernel timing totals since the last query (pic_tuning.timing = 1). */
+typedef struct pic_timing {
+    double particle_ms, field_ms, sort_ms;
+    int64_t particle_launches, field_launches, sort_launches;
+} pic_timing;
+
+/* Device memory hooks.  alloc returns a device pointer of `bytes` usable on
+   `stream` (NULL on failure); free releases it.  Without hooks the library
+   uses cudaMalloc / cudaFree.  Set before creating simulations. */
+typedef void *(*pic_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*pic_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn release, void *ctx);
+
+/* Create a simulation on the current CUDA device.  stream: a cudaStream_t
+   (NULL = the legacy default stream).  Checks dt against Eq. dtlimit with
+   no plasma yet (PIC_EDTLIMIT).  *out receives the handle. */
+pic_status pic_create(const pic_grid_desc *grid, void *stream, pic_sim **out);
+
+/* Free all device state of the handle (NULL is accepted). */
+pic_status pic_destroy(pic_sim *sim);
+
+/* Material mask (Sec. 3): n = number of cells, 1 = material, 0 = vacuum.
+   Must precede pic_load_species. */
+pic_status pic_set_material_mask(pic_sim *sim, const uint8_t *mask, size_t n);
+
+/* Add a species (explicit particles or the Fermi-Dirac loader) and sort it
+   into tiles.  Re-checks Eq. dtlimit with the plasma and binding frequencies
+   of all species so far (PIC_EDTLIMIT).  *species_id receives its index. */
+pic_status pic_load_species(pic_sim *sim, const pic_species_desc *desc,
+                            const pic_particles *parts, int *species_id);
+
+/* Set tuning; call before the first pic_step. */
+pic_status pic_set_tuning(pic_sim *sim, const pic_tuning *tuning);
+
+/* Enqueue nsteps PIC steps on the simulation's stream (asynchronous). */
+pic_status pic_step(pic_sim *sim, int nsteps);
+
+/* Wait for the stream; return a latched device error, if any. */
+pic_status pic_sync(pic_sim *sim);
+
+/* Copy fields to/from host FP64 arrays (converted from/to the FP32 device
+   fields).  which = OR of PIC_E*, PIC_B*, PIC_J*; the arrays of the selected
+   components follow one another in bit order, each ncell long; n = total
+   doubles.  J is readable only with keep_J.  Synchronous. */
+pic_status pic_read_fields(pic_sim *sim, int which, double *host_out, size_t n);
+pic_status pic_write_fields(pic_sim *sim, int which, const double *host_in, size_t n);
+
+/* Copy one species back in load order (particle id order): cell[n] linear
+   cell index, off[3n], v[3n]; for PIC_BOUND anchor_off[3n] and disp[3n]
+   (pass NULL for unused arrays).  n must equal the species count. */
+pic_status pic_read_species(pic_sim *sim, int species, int32_t *cell, float *off, float *v,
+                            double *anchor_off, float *disp, size_t n);
+
+/* Particles per cell of one species (current positions), int32[ncell]. */
+pic_status pic_cell_counts(pic_sim *sim, int species, int32_t *host_out, size_t n);
+
+/* FP64 diagnostics (kinetic and field energy, Gauss residual, counts). */
+pic_status pic_diagnostics(pic_sim *sim, pic_diag *out);
+
+/* Kernel timing totals since the last call; resets them.  Synchronous. */
+pic_status pic_get_timing(pic_sim *sim, pic_timing *out);
+
+/* Device bytes held by the handle. */
+pic_status pic_memory_bytes(const pic_sim *sim, size_t *bytes);
+
+/* Text of the last error on this handle (never NULL). */
+const char *pic_last_error(const pic_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,655 @@
+// k_particle.cu -- the particle phase of one PIC step, fused in one kernel:
+// CIC gather of E^n, B^n -> push (free: Boris; bound: modified Boris;
+// Dirac: Boris + |v| renormalised to v_F) -> specular reflection at material
+// edges -> Esirkepov charge-conserving current deposit.
+//
+// Paper passages: gather and deposit with the shape function W (Sec. 4.1);
+// free push Appendix A.1 (Eqs. borisvpm, borisrotsol, borisscheme); bound
+// push Sec. 4 Eq. modlorentz and Appendix A.2 (Eqs. modborisvpm,
+// modborisrotsol, modborisBrot); Dirac push Sec. 5; material boundary Sec. 3.
+//
+// Work decomposition: particles are sorted by tile (T0 x T1 x T2 cells).  A
+// persistent CTA takes tiles from the active-tile list; for each tile it
+// stages E^n and B^{n-1/2} of the tile plus a halo (cells -2 .. T+2 on each
+// axis) in shared memory, turns B^{n-1/2} into B^n = B^{n-1/2} - (dt/2)
+// curl E^n in place, zeroes a J tile of the same extent, and then streams the
+// tile's particles of every species: reads are coalesced SoA loads, the
+// gather reads shared memory, the deposit accumulates in the shared J tile
+// (shared-memory atomics: the per-tile reduction), and the J tile is flushed
+// to global memory with one atomic per non-zero entry.  A particle that has
+// drifted more than one cell out of its tile since the last sort takes a
+// slow path (global gather, global atomics), so correctness never depends on
+// how often the particles are re-sorted.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHalo = 2;  // box covers local cells [-2, T+2]
+constexpr int kMaxBlocksPerAxis = 16;  // field blocks a tile box may overlap per axis
+
+__device__ inline float clamp_below_one(float f) {
+    return f < 1.0f ? f : 0x1.fffffep-1f;
+}
+
+__device__ inline int wrap_or_neg(int i, int n, int per) {
+    if (i >= 0 && i < n) return i;
+    if (!per) return -1;
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// field access: shared-memory box (fast path) or global memory (slow path)
+// ---------------------------------------------------------------------------
+
+// Components: 0..2 E, 3..5 B^n.  Coordinates are "local" integers: box
+// coordinates (local cell + 2) for the box, global cell indices (possibly
+// outside [0,n)) for the global accessor.
+struct BoxAcc {
+    float *F[6];
+    float *J[3];
+    int b0, b01;
+    int hz;  // halo along z: 2 in 3D, 0 in 2D
+    // local cell coordinates (relative to the tile origin) -> box index
+    __device__ inline int idx(int x, int y, int z) const {
+        return (z + hz) * b01 + (y + kHalo) * b0 + (x + kHalo);
+    }
+    __device__ inline float get(int c, int x, int y, int z) const { return F[c][idx(x, y, z)]; }
+    __device__ inline void add(int c, int x, int y, int z, float v) const {
+        atomicAdd(&J[c][idx(x, y, z)], v);
+    }
+};
+
+template <int DIM>
+struct GlobalAcc {
+    const GridP *g;
+    const float *const *E;
+    const float *const *B;
+    float *const *J;
+    uint8_t *jdirty;
+    int nbx, nby, zchunk;
+    __device__ inline long long off(int x, int y, int z) const {
+        int gx = wrap_or_neg(x, g->n[0], g->per[0]);
+        int gy = wrap_or_neg(y, g->n[1], g->per[1]);
+        int gz = DIM == 3 ? wrap_or_neg(z, g->n[2], g->per[2]) : 0;
+        if (gx < 0 || gy < 0 || gz < 0) return -1;
+        return ((long long)gz * g->n[1] + gy) * g->n[0] + gx;
+    }
+    __device__ inline float e(int c, int x, int y, int z) const {
+        long long o = off(x, y, z);
+        return o < 0 ? 0.f : __ldg(E[c] + o);
+    }
+    __device__ inline float get(int c, int x, int y, int z) const {
+        if (c < 3) return e(c, x, y, z);
+        long long o = off(x, y, z);
+        if (o < 0) return 0.f;
+        const float h = 0.5f * g->dt;
+        float b = __ldg(B[c - 3] + o);
+        if (c == 3) {
+            float dEz_dy = (e(2, x, y + 1, z) - e(2, x, y, z)) * g->inv_d[1];
+            float dEy_dz = DIM == 3 ? (e(1, x, y, z + 1) - e(1, x, y, z)) * g->inv_d[2] : 0.f;
+            return b - h * (dEz_dy - dEy_dz);
+        } else if (c == 4) {
+            float dEx_dz = DIM == 3 ? (e(0, x, y, z + 1) - e(0, x, y, z)) * g->inv_d[2] : 0.f;
+            float dEz_dx = (e(2, x + 1, y, z) - e(2, x, y, z)) * g->inv_d[0];
+            return b - h * (dEx_dz - dEz_dx);
+        } else {
+            float dEy_dx = (e(1, x + 1, y, z) - e(1, x, y, z)) * g->inv_d[0];
+            float dEx_dy = (e(0, x, y + 1, z) - e(0, x, y, z)) * g->inv_d[1];
+            return b - h * (dEy_dx - dEx_dy);
+        }
+    }
+    __device__ inline void add(int c, int x, int y, int z, float v) const {
+        long long o = off(x, y, z);
+        if (o < 0) return;  // deposits beyond a wall are dropped
+        atomicAdd(J[c] + o, v);
+        int gx = (int)(o % g->n[0]);
+        int gy = (int)((o / g->n[0]) % g->n[1]);
+        int gz = (int)(o / ((long long)g->n[0] * g->n[1]));
+        int bz = DIM == 3 ? gz / zchunk : 0;
+        jdirty[((long long)bz * nby + gy / kFieldBY) * nbx + gx / kFieldBX] = 1;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// CIC gather on the Yee stagger
+// ---------------------------------------------------------------------------
+
+// Per axis: integer-staggered nodes (base, weight of base+1) and
+// half-staggered nodes.
+struct AxisW {
+    int bi, bh;
+    float wi, wh;
+};
+
+__device__ inline AxisW axis_weights(int l, float f) {
+    AxisW a;
+    a.bi = l;
+    a.wi = f;
+    float u = f - 0.5f;
+    if (u >= 0.f) {
+        a.bh = l;
+        a.wh = u;
+    } else {
+        a.bh = l - 1;
+        a.wh = u + 1.0f;
+    }
+    return a;
+}
+
+template <int DIM, class Acc>
+__device__ inline float interp(const Acc &A, int c, const AxisW *w, bool hx, bool hy, bool hz) {
+    int bx = hx ? w[0].bh : w[0].bi, by = hy ? w[1].bh : w[1].bi;
+    float x1 = hx ? w[0].wh : w[0].wi, y1 = hy ? w[1].wh : w[1].wi;
+    float x0 = 1.f - x1, y0 = 1.f - y1;
+    if (DIM == 2) {
+        return y0 * (x0 * A.get(c, bx, by, 0) + x1 * A.get(c, bx + 1, by, 0)) +
+               y1 * (x0 * A.get(c, bx, by + 1, 0) + x1 * A.get(c, bx + 1, by + 1, 0));
+    }
+    int bz = hz ? w[2].bh : w[2].bi;
+    float z1 = hz ? w[2].wh : w[2].wi, z0 = 1.f - z1;
+    float a0 = y0 * (x0 * A.get(c, bx, by, bz) + x1 * A.get(c, bx + 1, by, bz)) +
+               y1 * (x0 * A.get(c, bx, by + 1, bz) + x1 * A.get(c, bx + 1, by + 1, bz));
+    float a1 = y0 * (x0 * A.get(c, bx, by, bz + 1) + x1 * A.get(c, bx + 1, by, bz + 1)) +
+               y1 * (x0 * A.get(c, bx, by + 1, bz + 1) + x1 * A.get(c, bx + 1, by + 1, bz + 1));
+    return z0 * a0 + z1 * a1;
+}
+
+// E^n, B^n at a particle in cell (l[0..2]) with offsets f[0..2].
+template <int DIM, class Acc>
+__device__ inline void gather(const Acc &A, const int *l, const float *f, float *E, float *B) {
+    AxisW w[3];
+    w[0] = axis_weights(l[0], f[0]);
+    w[1] = axis_weights(l[1], f[1]);
+    w[2] = axis_weights(DIM == 3 ? l[2] : 0, DIM == 3 ? f[2] : 0.f);
+    E[0] = interp<DIM>(A, 0, w, true, false, false);
+    E[1] = interp<DIM>(A, 1, w, false, true, false);
+    E[2] = interp<DIM>(A, 2, w, false, false, true);
+    B[0] = interp<DIM>(A, 3, w, false, true, true);
+    B[1] = interp<DIM>(A, 4, w, true, false, true);
+    B[2] = interp<DIM>(A, 5, w, true, true, false);
+}
+
+// ---------------------------------------------------------------------------
+// Esirkepov deposit (order 1)
+// ---------------------------------------------------------------------------
+
+// Shape values on the three nodes lo, lo+1, lo+2 of one axis, at the start
+// (S0) and their change (DS) for a move from (c0, f0) to (c1, f1), |c1-c0| <= 1.
+__device__ inline void shape3(int c0, float f0, int c1, float f1, int lo, float *S0, float *DS) {
+    float s1[3];
+    if (c0 == lo) { S0[0] = 1.f - f0; S0[1] = f0; S0[2] = 0.f; }
+    else { S0[0] = 0.f; S0[1] = 1.f - f0; S0[2] = f0; }
+    if (c0 == c1) {
+        float d = f1 - f0;
+        if (c0 == lo) { DS[0] = -d; DS[1] = d; DS[2] = 0.f; }
+        else { DS[0] = 0.f; DS[1] = -d; DS[2] = d; }
+        return;
+    }
+    if (c1 == lo) { s1[0] = 1.f - f1; s1[1] = f1; s1[2] = 0.f; }
+    else { s1[0] = 0.f; s1[1] = 1.f - f1; s1[2] = f1; }
+    for (int m = 0; m < 3; ++m) DS[m] = s1[m] - S0[m];
+}
+
+template <int DIM, class Acc>
+__device__ inline void deposit(const Acc &A, const int *c0, const float *f0, const int *c1,
+                               const float *f1, const float *jf, float vz) {
+    float S0[3][3], DS[3][3];
+    int lo[3];
+    for (int a = 0; a < DIM; ++a) {
+        lo[a] = min(c0[a], c1[a]);
+        shape3(c0[a], f0[a], c1[a], f1[a], lo[a], S0[a], DS[a]);
+    }
+    const float third = 1.0f / 3.0f;
+    if (DIM == 3) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float T = S0[1][j] * S0[2][k] + 0.5f * DS[1][j] * S0[2][k] +
+                          0.5f * S0[1][j] * DS[2][k] + third * DS[1][j] * DS[2][k];
+                if (T == 0.f) continue;
+                float r0 = DS[0][0] * T, r1 = (DS[0][0] + DS[0][1]) * T;
+                if (r0 != 0.f) A.add(0, lo[0], lo[1] + j, lo[2] + k, jf[0] * r0);
+                if (r1 != 0.f) A.add(0, lo[0] + 1, lo[1] + j, lo[2] + k, jf[0] * r1);
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float T = S0[0][i] * S0[2][k] + 0.5f * DS[0][i] * S0[2][k] +
+                          0.5f * S0[0][i] * DS[2][k] + third * DS[0][i] * DS[2][k];
+                if (T == 0.f) continue;
+                float r0 = DS[1][0] * T, r1 = (DS[1][0] + DS[1][1]) * T;
+                if (r0 != 0.f) A.add(1, lo[0] + i, lo[1], lo[2] + k, jf[1] * r0);
+                if (r1 != 0.f) A.add(1, lo[0] + i, lo[1] + 1, lo[2] + k, jf[1] * r1);
+            }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float T = S0[0][i] * S0[1][j] + 0.5f * DS[0][i] * S0[1][j] +
+                          0.5f * S0[0][i] * DS[1][j] + third * DS[0][i] * DS[1][j];
+                if (T == 0.f) continue;
+                float r0 = DS[2][0] * T, r1 = (DS[2][0] + DS[2][1]) * T;
+                if (r0 != 0.f) A.add(2, lo[0] + i, lo[1] + j, lo[2], jf[2] * r0);
+                if (r1 != 0.f) A.add(2, lo[0] + i, lo[1] + j, lo[2] + 1, jf[2] * r1);
+            }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float T = S0[1][j] + 0.5f * DS[1][j];
+            if (T == 0.f) continue;
+            float r0 = DS[0][0] * T, r1 = (DS[0][0] + DS[0][1]) * T;
+            if (r0 != 0.f) A.add(0, lo[0], lo[1] + j, 0, jf[0] * r0);
+            if (r1 != 0.f) A.add(0, lo[0] + 1, lo[1] + j, 0, jf[0] * r1);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float T = S0[0][i] + 0.5f * DS[0][i];
+            if (T == 0.f) continue;
+            float r0 = DS[1][0] * T, r1 = (DS[1][0] + DS[1][1]) * T;
+            if (r0 != 0.f) A.add(1, lo[0] + i, lo[1], 0, jf[1] * r0);
+            if (r1 != 0.f) A.add(1, lo[0] + i, lo[1] + 1, 0, jf[1] * r1);
+        }
+        const float fz = jf[2] * vz;
+        if (fz != 0.f) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float W = S0[0][i] * S0[1][j] + 0.5f * DS[0][i] * S0[1][j] +
+                              0.5f * S0[0][i] * DS[1][j] + third * DS[0][i] * DS[1][j];
+                    if (W != 0.f) A.add(2, lo[0] + i, lo[1] + j, 0, fz * W);
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pushers
+// ---------------------------------------------------------------------------
+
+// Boris (Appendix A.1): v- = v + h E; v+ = [(1-|b|^2) v- + 2 b (v-.b) +
+// 2 v- x b] / (1 + |b|^2), b = h B; v = v+ + h E; h = q dt / (2m).
+__device__ inline void boris(float *v, const float *E, const float *B, float h) {
+    float vm0 = v[0] + h * E[0], vm1 = v[1] + h * E[1], vm2 = v[2] + h * E[2];
+    float b0 = h * B[0], b1 = h * B[1], b2 = h * B[2];
+    float bb = b0 * b0 + b1 * b1 + b2 * b2;
+    float vb = vm0 * b0 + vm1 * b1 + vm2 * b2;
+    float c0 = vm1 * b2 - vm2 * b1, c1 = vm2 * b0 - vm0 * b2, c2 = vm0 * b1 - vm1 * b0;
+    float inv = 1.0f / (1.0f + bb);
+    float s = 1.0f - bb;
+    v[0] = (s * vm0 + 2.f * (b0 * vb + c0)) * inv + h * E[0];
+    v[1] = (s * vm1 + 2.f * (b1 * vb + c1)) * inv + h * E[1];
+    v[2] = (s * vm2 + 2.f * (b2 * vb + c2)) * inv + h * E[2];
+}
+
+// Modified Boris for bound species (Appendix A.2, isotropic gamma):
+// kick = h E - (dt/2) w0^2 D; v- = v + kick; solve
+// (1 + g) v+ - v+ x b = (1 - g) v- + v- x b, g = gamma dt / 2, in closed form
+// v+ = (a^2 w + a (w x b) + (w.b) b) / (a (a^2 + |b|^2)), a = 1 + g,
+// w = (1 - g) v- + v- x b; v = v+ + kick; D += dt v.
+__device__ inline void bound_push(float *v, float *D, const float *E, const float *B,
+                                  const SpeciesP &s) {
+    const float h = s.hq;
+    float k0 = h * E[0] - s.hw0sq[0] * D[0];
+    float k1 = h * E[1] - s.hw0sq[1] * D[1];
+    float k2 = h * E[2] - s.hw0sq[2] * D[2];
+    float vm0 = v[0] + k0, vm1 = v[1] + k1, vm2 = v[2] + k2;
+    float b0 = h * B[0], b1 = h * B[1], b2 = h * B[2];
+    float a = 1.f + s.gdt2, cc = 1.f - s.gdt2;
+    float w0 = cc * vm0 + (vm1 * b2 - vm2 * b1);
+    float w1 = cc * vm1 + (vm2 * b0 - vm0 * b2);
+    float w2 = cc * vm2 + (vm0 * b1 - vm1 * b0);
+    float wb = w0 * b0 + w1 * b1 + w2 * b2;
+    float bb = b0 * b0 + b1 * b1 + b2 * b2;
+    float inv = 1.0f / (a * (a * a + bb));
+    float p0 = (a * a * w0 + a * (w1 * b2 - w2 * b1) + wb * b0) * inv;
+    float p1 = (a * a * w1 + a * (w2 * b0 - w0 * b2) + wb * b1) * inv;
+    float p2 = (a * a * w2 + a * (w0 * b1 - w1 * b0) + wb * b2) * inv;
+    v[0] = p0 + k0;
+    v[1] = p1 + k1;
+    v[2] = p2 + k2;
+    D[0] += s.dt * v[0];
+    D[1] += s.dt * v[1];
+    D[2] += s.dt * v[2];
+}
+
+// Dirac carriers (Sec. 5): Boris with the transverse mass, v_z = 0 (sheet in
+// the x-y plane), then |v| = v_F; a zero intermediate keeps the old direction.
+__device__ inline void dirac_push(float *v, const float *E, const float *B, const SpeciesP &s) {
+    float old0 = v[0], old1 = v[1], old2 = v[2];
+    boris(v, E, B, s.hq);
+    v[2] = 0.f;
+    float n2 = v[0] * v[0] + v[1] * v[1];
+    if (n2 > 0.f) {
+        float sc = s.vF / sqrtf(n2);
+        v[0] *= sc;
+        v[1] *= sc;
+    } else {
+        v[0] = old0;
+        v[1] = old1;
+        v[2] = old2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one particle
+// ---------------------------------------------------------------------------
+
+__device__ inline int mask_at(const ParticleLaunch &P, int x, int y, int z, bool &outside) {
+    const GridP &g = P.g;
+    int gx = wrap_or_neg(x, g.n[0], g.per[0]);
+    int gy = wrap_or_neg(y, g.n[1], g.per[1]);
+    int gz = g.dims == 3 ? wrap_or_neg(z, g.n[2], g.per[2]) : 0;
+    outside = gx < 0 || gy < 0 || gz < 0;
+    if (outside) return 0;
+    if (!P.mask) return 1;
+    return __ldg(P.mask + ((long long)gz * g.n[1] + gy) * g.n[0] + gx) != 0;
+}
+
+// Process particle p of species s.  org = tile origin (global cell), box
+// accessor for the fast path, global accessor for the slow path.
+template <int DIM>
+__device__ inline unsigned process_particle(const ParticleLaunch &P, const SpeciesP &s, long long p,
+                                            const int *org, const BoxAcc &box,
+                                            const GlobalAcc<DIM> &glob) {
+    const GridP &g = P.g;
+    const uint32_t pc = s.cell[p];
+    const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
+    // local cell relative to the tile origin, unwrapped across periodic edges
+    int lc[3];
+    for (int a = 0; a < 3; ++a) {
+        int l = gc[a] - org[a];
+        if (a < DIM && g.per[a]) {
+            int n = g.n[a];
+            if (l < -kHalo) l += n;
+            else if (l > P.tp.T[a] + kHalo) l -= n;
+        }
+        lc[a] = a < DIM ? l : 0;
+    }
+    float v[3] = {s.v[0][p], s.v[1][p], s.v[2][p]};
+    float E[3], B[3];
+    unsigned refl = 0;
+
+    if (s.kind == PIC_BOUND) {
+        // position = anchor cell + anchor offset (FP64) + displacement / d
+        float D[3] = {s.disp[0][p], s.disp[1][p], s.disp[2][p]};
+        int c0[3], c1[3];
+        float f0[3], f1[3];
+        double an[3];
+        for (int a = 0; a < 3; ++a) {
+            an[a] = (a < DIM) ? s.anchor[a][p] : 0.5;
+            double X = an[a] + (double)D[a] * (double)g.inv_d[a];
+            double fl = floor(X);
+            c0[a] = lc[a] + (int)fl;
+            f0[a] = (float)(X - fl);
+            if (a >= DIM) { c0[a] = 0; f0[a] = 0.f; }
+        }
+        bool fast = true;
+        for (int a = 0; a < DIM; ++a) fast = fast && c0[a] >= -1 && c0[a] <= P.tp.T[a];
+        if (fast) gather<DIM>(box, c0, f0, E, B);
+        else {
+            int gg[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
+            gather<DIM>(glob, gg, f0, E, B);
+        }
+        bound_push(v, D, E, B, s);
+        bool jump = false;
+        for (int a = 0; a < 3; ++a) {
+            double X = an[a] + (double)D[a] * (double)g.inv_d[a];
+            double fl = floor(X);
+            c1[a] = lc[a] + (int)fl;
+            f1[a] = clamp_below_one((float)(X - fl));
+            if (a >= DIM) { c1[a] = 0; f1[a] = 0.f; }
+            jump = jump || c1[a] - c0[a] > 1 || c0[a] - c1[a] > 1 || !(X == X);
+        }
+        if (jump) {
+            // more than one cell in one step (or NaN): record, deposit nothing
+            atomicOr(P.status, kStatusBounds);
+            for (int a = 0; a < 3; ++a) { c1[a] = c0[a]; f1[a] = f0[a]; }
+        }
+        if (fast) deposit<DIM>(box, c0, f0, c1, f1, s.jfac, v[2]);
+        else {
+            int g0[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
+            int g1[3] = {c1[0] + org[0], c1[1] + org[1], c1[2] + org[2]};
+            deposit<DIM>(glob, g0, f0, g1, f1, s.jfac, v[2]);
+        }
+        s.disp[0][p] = D[0];
+        s.disp[1][p] = D[1];
+        s.disp[2][p] = D[2];
+        s.v[0][p] = v[0];
+        s.v[1][p] = v[1];
+        s.v[2][p] = v[2];
+        return 0;
+    }
+
+    float f0[3] = {s.o[0][p], s.o[1][p], DIM == 3 ? s.o[2][p] : 0.f};
+    bool fast = true;
+    for (int a = 0; a < DIM; ++a) fast = fast && lc[a] >= -1 && lc[a] <= P.tp.T[a];
+    if (fast) gather<DIM>(box, lc, f0, E, B);
+    else gather<DIM>(glob, gc, f0, E, B);
+
+    if (s.kind == PIC_DIRAC) dirac_push(v, E, B, s);
+    else boris(v, E, B, s.hq);
+
+    // drift, cell change
+    float f1[3];
+    int sh[3] = {0, 0, 0};
+    bool moved = false;
+    for (int a = 0; a < 3; ++a) {
+        f1[a] = f0[a];
+        if (a >= DIM) continue;
+        float x = f0[a] + s.dtd[a] * v[a];
+        if (!(x > -1.f && x < 2.f)) {
+            // more than one cell in one step (or NaN): record and stay put
+            atomicOr(P.status, kStatusBounds);
+            x = f0[a];
+        }
+        if (x >= 1.f) { sh[a] = 1; x -= 1.f; }
+        else if (x < 0.f) { sh[a] = -1; x += 1.f; }
+        f1[a] = clamp_below_one(x);
+        moved = moved || sh[a] != 0;
+    }
+    if (moved) {
+        bool out1, out0;
+        int m1 = mask_at(P, gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2], out1);
+        int m0 = mask_at(P, gc[0], gc[1], gc[2], out0);
+        if (out1 || (m0 && !m1)) {
+            for (int a = 0; a < DIM; ++a) {
+                if (sh[a] == 0) continue;
+                f1[a] = clamp_below_one(1.f - f1[a]);
+                v[a] = -v[a];
+                sh[a] = 0;
+            }
+            refl = 1;
+        }
+    }
+    int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
+    if (fast) deposit<DIM>(box, lc, f0, c1l, f1, s.jfac, v[2]);
+    else {
+        int g1[3] = {gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2]};
+        deposit<DIM>(glob, gc, f0, g1, f1, s.jfac, v[2]);
+    }
+    if (sh[0] | sh[1] | sh[2]) {
+        int nxc[3];
+        for (int a = 0; a < 3; ++a) {
+            nxc[a] = gc[a] + sh[a];
+            if (a < DIM && g.per[a]) nxc[a] = wrap_or_neg(nxc[a], g.n[a], 1);
+        }
+        s.cell[p] = pack_cell(nxc[0], nxc[1], nxc[2]);
+    }
+    s.o[0][p] = f1[0];
+    s.o[1][p] = f1[1];
+    if (DIM == 3) s.o[2][p] = f1[2];
+    s.v[0][p] = v[0];
+    s.v[1][p] = v[1];
+    s.v[2][p] = v[2];
+    return refl;
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
+    extern __shared__ float smem[];
+    __shared__ unsigned s_refl[kMaxSpecies];
+    const TileP &tp = P.tp;
+    const int bn = tp.boxn;
+    BoxAcc box;
+    for (int c = 0; c < 6; ++c) box.F[c] = smem + c * bn;
+    for (int c = 0; c < 3; ++c) box.J[c] = smem + (6 + c) * bn;
+    box.b0 = tp.box[0];
+    box.b01 = tp.box[0] * tp.box[1];
+    box.hz = DIM == 3 ? kHalo : 0;
+    GlobalAcc<DIM> glob;
+    glob.g = &P.g;
+    glob.E = P.E;
+    glob.B = P.B;
+    glob.J = P.J;
+    glob.jdirty = P.jdirty;
+    glob.nbx = P.nbx;
+    glob.nby = P.nby;
+    glob.zchunk = P.zchunk;
+
+    if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.step_counter += 1;
+
+    const GridP &g = P.g;
+    const int nact = *P.nactive;
+    const float hdt = 0.5f * g.dt;
+    for (int it = blockIdx.x; it < nact; it += gridDim.x) {
+        const int t = P.active[it];
+        const int tx = t % tp.nt[0], ty = (t / tp.nt[0]) % tp.nt[1], tz = t / (tp.nt[0] * tp.nt[1]);
+        const int org[3] = {tx * tp.T[0], ty * tp.T[1], DIM == 3 ? tz * tp.T[2] : 0};
+        __syncthreads();  // previous tile's flush is done with the box
+        // stage E^n, B^{n-1/2} of the box; zero J
+        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+            bool in = gx >= 0 && gy >= 0 && gz >= 0;
+            long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
+            for (int c = 0; c < 3; ++c) {
+                box.F[c][e] = in ? __ldg(P.E[c] + o) : 0.f;
+                box.F[3 + c][e] = in ? __ldg(P.B[c] + o) : 0.f;
+                box.J[c][e] = 0.f;
+            }
+        }
+        __syncthreads();
+        // B^n = B^{n-1/2} - (dt/2) curl E^n (plain Yee curl); zero outside
+        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+            bool hx = bx + 1 < tp.box[0], hy = by + 1 < tp.box[1];
+            bool hz = DIM == 2 || bz + 1 < tp.box[2];
+            if (!(hx && hy && hz)) continue;  // never gathered
+            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+            if (gx < 0 || gy < 0 || gz < 0) {
+                box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
+                continue;
+            }
+            const int sx = 1, sy = box.b0, sz = box.b01;
+            float dEz_dy = (box.F[2][e + sy] - box.F[2][e]) * g.inv_d[1];
+            float dEx_dy = (box.F[0][e + sy] - box.F[0][e]) * g.inv_d[1];
+            float dEz_dx = (box.F[2][e + sx] - box.F[2][e]) * g.inv_d[0];
+            float dEy_dx = (box.F[1][e + sx] - box.F[1][e]) * g.inv_d[0];
+            float dEy_dz = 0.f, dEx_dz = 0.f;
+            if (DIM == 3) {
+                dEy_dz = (box.F[1][e + sz] - box.F[1][e]) * g.inv_d[2];
+                dEx_dz = (box.F[0][e + sz] - box.F[0][e]) * g.inv_d[2];
+            }
+            box.F[3][e] -= hdt * (dEz_dy - dEy_dz);
+            box.F[4][e] -= hdt * (dEx_dz - dEz_dx);
+            box.F[5][e] -= hdt * (dEy_dx - dEx_dy);
+        }
+        __syncthreads();
+        for (int si = 0; si < P.nsp; ++si) {
+            const SpeciesP &s = P.sp[si];
+            const long long a = s.tile_start[t], b = s.tile_start[t + 1];
+            unsigned r = 0;
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
+                r += process_particle<DIM>(P, s, p, org, box, glob);
+            }
+            if (r) atomicAdd(&s_refl[si], r);
+        }
+        __syncthreads();
+        // flush the J tile
+        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+            float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
+            if (jx == 0.f && jy == 0.f && jz == 0.f) continue;
+            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+            if (gx < 0 || gy < 0 || gz < 0) continue;
+            long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+            if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
+            if (jy != 0.f) atomicAdd(P.J[1] + o, jy);
+            if (jz != 0.f) atomicAdd(P.J[2] + o, jz);
+        }
+        // mark the field blocks the box overlaps
+        if (threadIdx.x == 0) {
+            int bl[3][kMaxBlocksPerAxis], nb[3];
+            const int fb[3] = {kFieldBX, kFieldBY, P.zchunk};
+            for (int ax = 0; ax < 3; ++ax) {
+                nb[ax] = 0;
+                if (ax == 2 && DIM == 2) { bl[2][0] = 0; nb[2] = 1; continue; }
+                for (int c = org[ax] - kHalo; c < org[ax] + tp.T[ax] + kHalo + 1; ++c) {
+                    int gc = wrap_or_neg(c, g.n[ax], g.per[ax]);
+                    if (gc < 0) continue;
+                    int blk = gc / fb[ax];
+                    bool seen = false;
+                    for (int q = 0; q < nb[ax]; ++q) seen = seen || bl[ax][q] == blk;
+                    if (!seen) {
+                        if (nb[ax] < kMaxBlocksPerAxis) bl[ax][nb[ax]++] = blk;
+                        else atomicOr(P.status, kStatusBounds);
+                    }
+                }
+            }
+            for (int z = 0; z < nb[2]; ++z)
+                for (int y = 0; y < nb[1]; ++y)
+                    for (int x = 0; x < nb[0]; ++x)
+                        P.jdirty[((long long)bl[2][z] * P.nby + bl[1][y]) * P.nbx + bl[0][x]] = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
+        atomicAdd(P.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
+}
+
+}  // namespace
+
+size_t particle_smem_bytes(const TileP &tp) { return (size_t)9 * tp.boxn * sizeof(float); }
+
+cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm) {
+    cudaError_t e;
+    if (dims == 3) {
+        e = cudaFuncSetAttribute(particle_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<3>,
+                                                             kThreads, smem);
+    }
+    e = cudaFuncSetAttribute(particle_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<2>, kThreads,
+                                                         smem);
+}
+
+cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s) {
+    if (nctas < 1) nctas = 1;
+    if (pl.g.dims == 3) particle_kernel<3><<<nctas, kThreads, smem, s>>>(pl);
+    else particle_kernel<2><<<nctas, kThreads, smem, s>>>(pl);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,240 @@
+// k_sort.cu -- counting sort of particles by tile, prefix sums, the active
+// tile list and per-cell particle counts.
+//
+// The sort keeps each species' SoA arrays grouped by particle tile so that
+// one CTA of the particle kernel finds the particles of its tile in one
+// contiguous range (tile_start[t] .. tile_start[t+1]).  Order inside a tile
+// is the order in which warps claimed slots (it carries no meaning).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+namespace {
+
+__device__ inline int tile_of(const TileP &tp, uint32_t c) {
+    int tx = cell_x(c) / tp.T[0], ty = cell_y(c) / tp.T[1], tz = cell_z(c) / tp.T[2];
+    return (tz * tp.nt[1] + ty) * tp.nt[0] + tx;
+}
+
+// count[t] += particles of tile t; rank[p] = slot of p inside its tile.
+// Warp-aggregated: lanes with the same tile share one atomic.
+__global__ void tile_hist_kernel(TileP tp, const uint32_t *cell, long long n, int *count,
+                                 int *rank) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+        long long p = base + threadIdx.x;
+        bool valid = p < n;
+        unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
+        int t = tile_of(tp, cell[p]);
+        unsigned m = __match_any_sync(vm, t);
+        int leader = __ffs(m) - 1;
+        int b = 0;
+        if (lane == leader) b = atomicAdd(&count[t], __popc(m));
+        b = __shfl_sync(m, b, leader);
+        rank[p] = b + __popc(m & ((1u << lane) - 1u));
+    }
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ inline int block_excl_scan(int v, int *total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int before = w > 0 ? warp_sums[w - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void scan_reduce_kernel(const int *in, long long n, int *sums) {
+    long long base = (long long)blockIdx.x * kScanChunk;
+    int s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        long long i = base + (long long)threadIdx.x * kScanItems + k;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// out[i] = offsets[block] + exclusive scan inside the block; out[n] = total
+__global__ void scan_down_kernel(const int *in, long long n, const int *offsets, int *out) {
+    long long base = (long long)blockIdx.x * kScanChunk;
+    int v[kScanItems];
+    int s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        long long i = base + (long long)threadIdx.x * kScanItems + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int pre = block_excl_scan(s, &total) + (offsets ? offsets[blockIdx.x] : 0);
+    for (int k = 0; k < kScanItems; ++k) {
+        long long i = base + (long long)threadIdx.x * kScanItems + k;
+        if (i < n) out[i] = pre;
+        pre += v[k];
+        if (i == n - 1) out[n] = pre;
+    }
+}
+
+template <class T>
+__device__ inline void mv(T *dst, const T *src, long long d, long long s) {
+    dst[d] = src[s];
+}
+
+__global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_src, SpeciesP dst,
+                                    uint32_t *pid_dst, const int *start, const int *rank) {
+    const long long n = src.n;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        uint32_t c = src.cell[p];
+        long long d = (long long)start[tile_of(tp, c)] + rank[p];
+        dst.cell[d] = c;
+        pid_dst[d] = pid_src[p];
+        for (int a = 0; a < 3; ++a) mv(dst.v[a], src.v[a], d, p);
+        if (src.kind == PIC_BOUND) {
+            for (int a = 0; a < 3; ++a) {
+                mv(const_cast<double *>(dst.anchor[a]), src.anchor[a], d, p);
+                mv(dst.disp[a], src.disp[a], d, p);
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) mv(dst.o[a], src.o[a], d, p);
+        }
+    }
+}
+
+__global__ void active_flags_kernel(TileP tp, const int *const *starts, int nsp, int *flags) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tp.ntiles; t += gridDim.x * blockDim.x) {
+        int any = 0;
+        for (int s = 0; s < nsp; ++s) any |= (starts[s][t + 1] - starts[s][t]) > 0;
+        flags[t] = any;
+    }
+}
+
+__global__ void active_scatter_kernel(int ntiles, const int *flags, const int *pos, int *active,
+                                      int *nactive) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        if (flags[t]) active[pos[t]] = t;
+        if (t == ntiles - 1) *nactive = pos[ntiles];
+    }
+}
+
+__global__ void cell_hist_kernel(GridP g, SpeciesP sp, int *counts) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < sp.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        uint32_t c = sp.cell[p];
+        int x[3] = {cell_x(c), cell_y(c), cell_z(c)};
+        if (sp.kind == PIC_BOUND) {
+            for (int a = 0; a < g.dims; ++a) {
+                double X = sp.anchor[a][p] + (double)sp.disp[a][p] * (double)g.inv_d[a];
+                x[a] += (int)floor(X);
+                if (g.per[a]) x[a] = (x[a] % g.n[a] + g.n[a]) % g.n[a];
+            }
+        }
+        bool in = true;
+        for (int a = 0; a < 3; ++a) in = in && x[a] >= 0 && x[a] < g.n[a];
+        if (in) atomicAdd(&counts[((long long)x[2] * g.n[1] + x[1]) * g.n[0] + x[0]], 1);
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_tile_histogram(const GridP &g, const TileP &tp, const uint32_t *cell,
+                                  long long n, int *count, int *rank, cudaStream_t s) {
+    (void)g;
+    if (n <= 0) return cudaSuccess;
+    tile_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(tp, cell, n, count, rank);
+    return cudaGetLastError();
+}
+
+long long scan_tmp_len(long long n) {
+    long long nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb <= 1) return 1;
+    return nb + (nb + 1) + scan_tmp_len(nb);
+}
+
+// Exclusive scan of n ints: out[0..n] (out[n] = total).  tmp: scan_tmp_len(n).
+cudaError_t launch_scan_int(const int *in, int *out_excl, long long n, int *tmp, long long tmp_len,
+                            cudaStream_t s) {
+    (void)tmp_len;
+    if (n <= 0) {
+        return cudaMemsetAsync(out_excl, 0, sizeof(int), s);
+    }
+    long long nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb == 1) {
+        scan_down_kernel<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out_excl);
+        return cudaGetLastError();
+    }
+    int *sums = tmp;
+    int *sums_scan = tmp + nb;  // nb + 1 entries ... recursion uses the rest
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // scan of the block sums into sums_scan (needs its own tmp beyond it)
+    e = launch_scan_int(sums, sums_scan, nb, sums_scan + nb + 1, 0, s);
+    if (e != cudaSuccess) return e;
+    scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums_scan, out_excl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
+                                const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
+                                const int *start, const int *rank, cudaStream_t s) {
+    (void)g;
+    if (src.n <= 0) return cudaSuccess;
+    tile_scatter_kernel<<<grid_for(src.n, 256), 256, 0, s>>>(tp, src, pid_src, dst, pid_dst, start,
+                                                             rank);
+    return cudaGetLastError();
+}
+
+// flags / positions live in `work`: 2 * (ntiles + 1) + scan_tmp_len(ntiles) ints
+cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,
+                                     int *active, int *nactive, int *work, cudaStream_t s) {
+    int *flags = work;
+    int *pos = work + tp.ntiles + 1;
+    int *tmp = pos + tp.ntiles + 1;
+    active_flags_kernel<<<grid_for(tp.ntiles, 256), 256, 0, s>>>(tp, starts_dev, nsp, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_scan_int(flags, pos, tp.ntiles, tmp, scan_tmp_len(tp.ntiles), s);
+    if (e != cudaSuccess) return e;
+    active_scatter_kernel<<<grid_for(tp.ntiles, 256), 256, 0, s>>>(tp.ntiles, flags, pos, active,
+                                                                  nactive);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_histogram(const GridP &g, const SpeciesP &sp, int *counts, cudaStream_t s) {
+    if (sp.n <= 0) return cudaSuccess;
+    cell_hist_kernel<<<grid_for(sp.n, 256), 256, 0, s>>>(g, sp, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

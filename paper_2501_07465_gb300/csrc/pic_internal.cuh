@@ -1,0 +1,184 @@
+// pic_internal.cuh -- device-side data layout and kernel parameter blocks of
+// the PIC step.  Shared by the CUDA translation units of libpic.so only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic.h"
+
+namespace pic {
+
+// SI constants (exact c; eps0 from CODATA 2018; mu0 from c and eps0).
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKB = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+
+// Particle cells are packed (x | y << 11 | z << 22): no integer division in
+// the hot loop.  Hence nx, ny <= 2048 and nz <= 1024.
+constexpr int kPackBitsX = 11, kPackBitsY = 11;
+__host__ __device__ inline uint32_t pack_cell(int x, int y, int z) {
+    return (uint32_t)x | ((uint32_t)y << kPackBitsX) | ((uint32_t)z << (kPackBitsX + kPackBitsY));
+}
+__host__ __device__ inline int cell_x(uint32_t c) { return (int)(c & 2047u); }
+__host__ __device__ inline int cell_y(uint32_t c) { return (int)((c >> 11) & 2047u); }
+__host__ __device__ inline int cell_z(uint32_t c) { return (int)(c >> 22); }
+
+// Device status word bits (latched, read at sync points).
+enum : int { kStatusBounds = 1, kStatusTimeout = 2 };
+
+struct GridP {
+    int dims;
+    int n[3];
+    int per[3];          // 1 = periodic axis
+    float d[3];          // cell size (m)
+    float inv_d[3];
+    float dt;
+    long long ncell;
+};
+
+// Per-species parameters of the particle kernel (FP32 coefficients are
+// formed on the host in FP64 and rounded once).
+struct SpeciesP {
+    int kind;
+    long long n;
+    uint32_t *cell;               // packed cell (anchor cell for bound)
+    float *o[3];                  // in-cell offset (free, Dirac)
+    float *v[3];                  // velocity (m/s)
+    const double *anchor[3];      // bound: anchor offset in [0,1), FP64
+    float *disp[3];               // bound: displacement from the anchor (m)
+    const int *tile_start;        // [ntiles + 1]
+    float hq;                     // q dt / (2 m)
+    float hw0sq[3];               // (dt/2) omega0^2 per axis
+    float gdt2;                   // gamma dt / 2
+    float vF;
+    float dt;
+    float dtd[3];                 // dt / d_a
+    float jfac[3];                // Esirkepov factors -q w / (d_b d_c dt); 2D J_z: q w / V
+    unsigned long long *nrefl;    // device reflection counter
+};
+
+struct FieldP {
+    const float *E[3];   // E^n (read)
+    const float *B[3];   // B^{n-1/2} (read)
+    float *En[3];        // E^{n+1} (write)
+    float *Bn[3];        // B^{n+1/2} (write)
+    float *J[3];         // J^{n+1/2}, zeroed after use unless keepJ
+    const uint8_t *jdirty;   // field-block flags: J may be non-zero
+    uint8_t *jdirty_clear;   // same array, cleared after use
+    // CPML: per PML axis a, slab arrays psi[a][c] (c = 0..3) ping-pong
+    //   axis x: E_y, E_z, B_y, B_z ; axis y: E_x, E_z, B_x, B_z ; axis z: E_x, E_y, B_x, B_y
+    const float *psi_in[3][4];
+    float *psi_out[3][4];
+    int pml[3];          // 1 = PML axis
+    int P;               // slab thickness
+    const float *cb_e[3], *ca_e[3], *cb_h[3], *ca_h[3];   // per-axis coefficients (length n_a)
+    // source
+    int src_on, inc, pol, src_index;
+    double src_amp;      // -2 E0 / (eta0 d_inc)
+    double src_omega, src_tau, src_t0;
+    const long long *step_counter;   // particle phases completed (step n -> n + 1)
+    double dt64;
+    float c2dt;          // c^2 dt
+    float dt_eps0;       // dt / eps0
+    int keepJ;
+    int zchunk;
+    int nbx, nby, nbz;   // field-block grid (for jdirty)
+};
+
+constexpr int kFieldBX = 32, kFieldBY = 8;
+
+// Particle tiling.
+struct TileP {
+    int T[3];        // tile dims (cells)
+    int nt[3];       // tiles per axis
+    int ntiles;
+    int box[3];      // staged box dims = T + 5 (3D) / T + 5, T + 5, 1 (2D)
+    int boxn;        // product
+};
+
+constexpr int kMaxSpecies = PIC_MAX_SPECIES;
+
+struct ParticleLaunch {
+    GridP g;
+    TileP tp;
+    int nsp;
+    SpeciesP sp[kMaxSpecies];
+    const float *E[3];
+    const float *B[3];       // B^{n-1/2}
+    float *J[3];
+    const uint8_t *mask;     // may be null (all material)
+    uint8_t *jdirty;
+    int nbx, nby, nbz, zchunk;
+    const int *active;       // active tile list
+    const int *nactive;
+    long long *step_counter;
+    int *status;
+};
+
+// ---------------------------------------------------------------------------
+// host-side launch wrappers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
+size_t particle_smem_bytes(const TileP &tp);
+cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm);
+
+// sort (k_sort.cu)
+cudaError_t launch_tile_histogram(const GridP &g, const TileP &tp, const uint32_t *cell,
+                                  long long n, int *count, int *rank, cudaStream_t s);
+cudaError_t launch_scan_int(const int *in, int *out_excl, long long n, int *tmp,
+                            long long tmp_len, cudaStream_t s);
+long long scan_tmp_len(long long n);
+cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
+                                const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
+                                const int *start, const int *rank, cudaStream_t s);
+cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,
+                                     int *active, int *nactive, int *work, cudaStream_t s);
+cudaError_t launch_cell_histogram(const GridP &g, const SpeciesP &sp, int *counts,
+                                  cudaStream_t s);
+
+// loader (k_fd.cu)
+struct FDRequest {
+    int kind, dims, ppc, quiet;
+    double m, mu, kT, vF;
+    uint64_t seed;
+    uint32_t stream;
+};
+constexpr int kFDPanels = 4096;
+double fd_pmax(const FDRequest &r);
+cudaError_t launch_fd_table(const FDRequest &r, double *table, double pmax, cudaStream_t s);
+cudaError_t launch_fd_particles(const GridP &g, const FDRequest &r, const int *mat_cells,
+                                long long np, const double *table, double pmax, SpeciesP out,
+                                uint32_t *pid, cudaStream_t s);
+cudaError_t launch_material_cells(const GridP &g, const uint8_t *mask, const int *rank,
+                                  int *mat_cells, cudaStream_t s);
+cudaError_t launch_mask_to_int(const uint8_t *mask, long long n, int *out, cudaStream_t s);
+
+// diagnostics (k_diag.cu)
+struct DiagAcc {
+    double kinetic[kMaxSpecies];
+    double e2, b2;
+    unsigned long long gauss_max_bits, rho_max_bits;
+    double gauss_sum2;
+};
+cudaError_t launch_kinetic(const SpeciesP &sp, double mw_half, double *acc, cudaStream_t s);
+cudaError_t launch_field_energy(const GridP &g, const float *const *E, const float *const *B,
+                                DiagAcc *acc, cudaStream_t s);
+cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V,
+                               double *rho, cudaStream_t s);
+cudaError_t launch_gauss(const GridP &g, const float *const *E, const double *rho,
+                         const double *rho_bg, DiagAcc *acc, cudaStream_t s);
+cudaError_t launch_add_uniform(double *rho, long long n, double v, cudaStream_t s);
+
+// readback helpers (k_diag.cu)
+cudaError_t launch_unsort(const GridP &g, const SpeciesP &sp, const uint32_t *pid,
+                          int32_t *cell_out, float *off_out, float *v_out, double *anchor_out,
+                          float *disp_out, cudaStream_t s);
+cudaError_t launch_pack_explicit(const GridP &g, long long n, const int32_t *cell_lin,
+                                 uint32_t *cell_packed, uint32_t *pid, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double *in, float *out, long long n, cudaStream_t s);
+
+}  // namespace pic

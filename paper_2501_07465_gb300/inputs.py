@@ -1,0 +1,218 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the
+benchmark: grid and species parameters of the workloads, material masks,
+random particle sets, initial fields.
+
+This module holds none of the PIC method's arithmetic (no push, gather,
+deposit, field update or Fermi-Dirac sampling) and imports nothing from the
+CUDA binding or the oracle, so that both sides can be fed the same arrays.
+
+Workloads (the paper's metal / graphene settings, Secs. 2-5):
+  langmuir2d  2D3V periodic 64 x 64, dx = 0.1 nm, 16 ppc free electrons
+              (n = 8.5e28 m^-3, E_F = 7.0 eV, 300 K, quiet 4 x 4 lattice),
+              uniform ions, 1 % sinusoidal density ripple along x,
+              dt = 0.5 dx / (c sqrt 2), 1000 steps.
+  sphere3d    256^3, dx = 0.5 nm, CPML 16 on all faces, sphere of radius
+              20 nm: 8 ppc free electrons (n = 5.9e28, E_F = 5.5 eV, 300 K)
+              + 8 ppc bound electrons (w0 = 2 pi c / 400 nm, gamma = 1e14,
+              N_b = 0.5 n), pulse lambda = 520 nm, 10 fs FWHM, 1e8 V/m,
+              dt = 0.5 dx / (c sqrt 3), 4000 steps.
+  graphene3d  512 x 512 x 64, dx = 1 nm, periodic x/y, CPML 16 along z, a
+              one-cell sheet at z = 32 with 32 ppc Dirac carriers
+              (v_F = 1e6, n_s = 1e16 m^-2, E_F = 0.2 eV, 300 K), normally
+              incident 10 THz pulse of 1e6 V/m, dt = 0.5 dx / (c sqrt 3),
+              2000 steps.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+C_LIGHT = 299792458.0
+EPS0 = 8.8541878128e-12
+HBAR = 1.054571817e-34
+SEED_BASE = 250107465
+
+FREE, BOUND, DIRAC = 0, 1, 2
+
+
+def grid_shape(n):
+    """(nz, ny, nx) array shape of a grid with n = (nx, ny, nz)."""
+    return (n[2], n[1], n[0])
+
+
+# ---------------------------------------------------------------------------
+# masks
+# ---------------------------------------------------------------------------
+
+def sphere_mask(n, radius_cells, center=None):
+    """1 inside a sphere (cell centres within radius_cells of center)."""
+    nx, ny, nz = n
+    c = center if center is not None else (nx / 2, ny / 2, nz / 2)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r2 = (i + 0.5 - c[0]) ** 2 + (j + 0.5 - c[1]) ** 2 + (k + 0.5 - c[2]) ** 2
+    return (r2 < radius_cells ** 2).astype(np.uint8)
+
+
+def sheet_mask(n, k0):
+    """1 on the plane of cells z = k0."""
+    m = np.zeros(grid_shape(n), np.uint8)
+    m[k0] = 1
+    return m
+
+
+def disk_mask2d(n, center, radius):
+    nx, ny = n[0], n[1]
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    return (((i + 0.5 - center[0]) ** 2 + (j + 0.5 - center[1]) ** 2) < radius ** 2).astype(
+        np.uint8)[None]
+
+
+def rod_mask2d(n, center, length, width):
+    nx, ny = n[0], n[1]
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    return ((np.abs(i + 0.5 - center[0]) < length / 2) &
+            (np.abs(j + 0.5 - center[1]) < width / 2)).astype(np.uint8)[None]
+
+
+def bowtie_mask2d(n, center, size, gap):
+    """Two triangles pointing at each other along x with a gap (cells)."""
+    nx, ny = n[0], n[1]
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    x = i + 0.5 - center[0]
+    y = j + 0.5 - center[1]
+    ax = np.abs(x) - gap / 2
+    inside = (ax >= 0) & (ax <= size) & (np.abs(y) <= ax * 0.6)
+    return inside.astype(np.uint8)[None]
+
+
+# ---------------------------------------------------------------------------
+# particles
+# ---------------------------------------------------------------------------
+
+def cell_coords(cell, n):
+    """Linear cell index -> (N, 3) integer coordinates (x fastest)."""
+    cell = np.asarray(cell, np.int64)
+    cz, rem = np.divmod(cell, n[0] * n[1])
+    cy, cx = np.divmod(rem, n[0])
+    return np.stack([cx, cy, cz], 1)
+
+
+def positions(cell, off, n):
+    """Cell index + in-cell offset -> position in cell units (float64)."""
+    return cell_coords(cell, n).astype(np.float64) + np.asarray(off, np.float64)
+
+
+def random_particles(rng, n, count, mask=None, vscale=1e6, dims=3, cells=None):
+    """`count` particles in uniformly chosen (material) cells: int32 cell,
+    float32 offsets in [0,1), float32 Gaussian velocities of scale vscale.
+    In 2D the z offset is 0.5 and v_z is kept (2D3V)."""
+    if cells is None:
+        ncell = n[0] * n[1] * n[2]
+        pool = np.arange(ncell) if mask is None else np.flatnonzero(np.asarray(mask).ravel())
+        cells = rng.choice(pool, size=count)
+    cell = np.asarray(cells, np.int32)
+    off = rng.random((count, 3)).astype(np.float32)
+    off = np.minimum(off, np.float32(np.nextafter(np.float32(1), np.float32(0))))
+    if dims == 2:
+        off[:, 2] = 0.5
+    v = (rng.normal(size=(count, 3)) * vscale).astype(np.float32)
+    return cell, off, v
+
+
+def random_bound(rng, n, count, mask=None, dscale=1e-12, vscale=1e4):
+    """Bound particles: int32 anchor cell, float64 anchor offsets,
+    float32 displacements (m) and velocities."""
+    ncell = n[0] * n[1] * n[2]
+    pool = np.arange(ncell) if mask is None else np.flatnonzero(np.asarray(mask).ravel())
+    cell = rng.choice(pool, size=count).astype(np.int32)
+    anchor = rng.random((count, 3))
+    disp = (rng.normal(size=(count, 3)) * dscale).astype(np.float32)
+    v = (rng.normal(size=(count, 3)) * vscale).astype(np.float32)
+    return cell, anchor, disp, v
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def fermi_velocity(E_F, m=ME):
+    return math.sqrt(2 * E_F / m)
+
+
+def langmuir2d(nx=64, ny=64, ppc=16, steps=1000):
+    dx = 0.1e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(2))
+    n0 = 8.5e28
+    return {
+        "name": f"langmuir2d {nx}x{ny} {ppc}ppc",
+        "grid": dict(dims=2, n=(nx, ny, 1), d=(dx, dx, dx), dt=dt, bc=(0, 0, 0), pml_cells=0),
+        "species": [dict(kind=FREE, q=-QE, m=ME, density=n0, E_F=7.0 * QE, T=300.0, ppc=ppc,
+                         quiet=1, background=2, seed=SEED_BASE + 0, stream=0)],
+        "mask": None,
+        "steps": steps,
+        "ripple": 0.01,
+    }
+
+
+def langmuir_ripple(X, nx, dx, amplitude):
+    """Displace x by -(A/k) sin(kx) (cell units), k = 2 pi / (nx dx): a
+    density ripple n0 (1 + A cos kx) to first order."""
+    k = 2 * math.pi / (nx * dx)
+    Y = np.array(X, dtype=np.float64, copy=True)
+    Y[:, 0] = Y[:, 0] - amplitude / (k * dx) * np.sin(k * Y[:, 0] * dx)
+    Y[:, 0] = np.mod(Y[:, 0], nx)
+    return Y
+
+
+def langmuir_initial_Ex(nx, ny, dx, n0, amplitude):
+    """E_x(i+1/2) = -(e n0 A / (eps0 k)) sin(k (i+1/2) dx) for electrons of
+    charge -e (Gauss's law of the ripple with a uniform ion background)."""
+    k = 2 * math.pi / (nx * dx)
+    i = np.arange(nx)
+    ex = -(QE * n0 * amplitude / (EPS0 * k)) * np.sin(k * (i + 0.5) * dx)
+    return np.broadcast_to(ex, (1, ny, nx)).copy()
+
+
+def sphere3d(n=256, radius_nm=20.0, ppc=8, steps=4000, pml=16):
+    dx = 0.5e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(3))
+    lam = 520e-9
+    nfree = 5.9e28
+    w0 = 2 * math.pi * C_LIGHT / 400e-9
+    return {
+        "name": f"sphere3d {n}^3 r={radius_nm}nm {ppc}+{ppc}ppc",
+        "grid": dict(dims=3, n=(n, n, n), d=(dx, dx, dx), dt=dt, bc=(1, 1, 1), pml_cells=pml,
+                     src=dict(inc_axis=0, pol_axis=1, src_index=pml + 2, E0=1e8,
+                              omega=2 * math.pi * C_LIGHT / lam, tau=10e-15, t0=1.0e-15)),
+        "mask": sphere_mask((n, n, n), radius_nm * 1e-9 / dx),
+        "species": [
+            dict(kind=FREE, q=-QE, m=ME, density=nfree, E_F=5.5 * QE, T=300.0, ppc=ppc, quiet=0,
+                 background=1, seed=SEED_BASE + 1, stream=0),
+            dict(kind=BOUND, q=-QE, m=ME, density=0.5 * nfree, E_F=0.0, T=0.0, ppc=ppc,
+                 quiet=1, background=1, seed=SEED_BASE + 1, stream=1, omega0=(w0, w0, w0),
+                 gamma=(1e14, 1e14, 1e14)),
+        ],
+        "steps": steps,
+    }
+
+
+def graphene3d(nx=512, ny=512, nz=64, ppc=32, steps=2000, pml=16):
+    dx = 1e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(3))
+    vF = 1e6
+    E_F = 0.2 * QE
+    m_d = (E_F / vF) / (2 * vF)  # averaged transverse mass p_F / (2 v_F), Sec. 5
+    n_s = 1e16
+    return {
+        "name": f"graphene3d {nx}x{ny}x{nz} {ppc}ppc",
+        "grid": dict(dims=3, n=(nx, ny, nz), d=(dx, dx, dx), dt=dt, bc=(0, 0, 1), pml_cells=pml,
+                     src=dict(inc_axis=2, pol_axis=0, src_index=pml + 2, E0=1e6,
+                              omega=2 * math.pi * 10e12, tau=200e-15, t0=0.0)),
+        "mask": sheet_mask((nx, ny, nz), nz // 2),
+        "species": [dict(kind=DIRAC, q=-QE, m=m_d, v_F=vF, density=n_s / dx, E_F=E_F, T=300.0,
+                         ppc=ppc, quiet=0, background=1, seed=SEED_BASE + 2, stream=0)],
+        "steps": steps,
+    }
