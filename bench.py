@@ -1,0 +1,482 @@
+"""Benchmark of the GB300 PIC step (one JSON line on stdout).
+
+Workload at N = 1: the 3D metal nanosphere (256^3 Yee grid, dx = 0.5 nm,
+CPML 16, sphere of radius 20 nm with 8 ppc Fermi-Dirac free electrons and
+8 ppc Lorentz-bound electrons, 520 nm pulse): one step = particle kernel +
+field kernel (+ a tile re-sort every 32 steps), timed with CUDA events on
+the simulation's stream.  Inputs (805 MB of ping-pong fields, 250 MB of
+particles) are larger than the 129 MB L2, so no flush is needed between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload.  Under torchrun with N > 1
+every rank runs an independent replica (the single simulation has no data
+exchange between GPUs: replicas only); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s & HBM-roofline %, FP32 vs FP64; batched sims/hr, p99 latency"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=256, help="cells per side (256 = the workload)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index, path=None):
+        self.gpu = gpu_index
+        self.path = path
+        self.proc = None
+        self.fh = None
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w") if self.path else subprocess.PIPE
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        if self.path:
+            self.fh.close()
+            out = open(self.path).read()
+        self.lines = [ln for ln in (out or "").splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# byte model (algorithmic bytes per launch)
+# ---------------------------------------------------------------------------
+
+def dilate(mask, r):
+    """Binary dilation by r cells along each axis (separable, periodic)."""
+    m = mask.astype(bool)
+    for ax in range(m.ndim):
+        if m.shape[ax] == 1:
+            continue
+        acc = m.copy()
+        for s in range(1, r + 1):
+            acc |= np.roll(m, s, axis=ax) | np.roll(m, -s, axis=ax)
+        m = acc
+    return m
+
+
+def field_bytes(wl):
+    """Field kernel: E, B read + write (48 B/cell), CPML psi read + write
+    (4 slots x 8 B per slab cell per PML axis), J read + zero (24 B) where a
+    deposit can reach (material cells dilated by 2)."""
+    g = wl["grid"]
+    nx, ny, nz = g["n"]
+    ncell = nx * ny * nz
+    b = 48 * ncell
+    P = g.get("pml_cells", 0)
+    for a in range(3):
+        if g["bc"][a] == 1 and (a < 2 or g["dims"] == 3):
+            b += 32 * 2 * P * ncell // g["n"][a]
+    mask = wl["mask"]
+    jcells = int(dilate(mask, 2).sum()) if mask is not None else ncell
+    b += 24 * jcells
+    return b, jcells
+
+
+def particle_bytes(nfree, nbound, nmat):
+    """Particle kernel: free 3D particle reads cell + 3 offsets + 3 v (28 B),
+    writes 3 offsets + 3 v (24 B); bound reads cell + 3 FP64 anchors + 3
+    displacements + 3 v (52 B), writes displacement + v (24 B); plus E, B
+    read (24 B) and J written (12 B) over the material cells."""
+    return nfree * 52 + nbound * 76 + 36 * nmat
+
+
+def traffic_from_profile(kernel_name, src_file):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}_sphere3d.md")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()
+    txt = open(path).read()
+    got_sha = None
+    val = None
+    for ln in txt.splitlines():
+        if ln.startswith("source_sha256:"):
+            got_sha = ln.split(":", 1)[1].strip()
+        if ln.startswith("dram_bytes_per_launch:"):
+            try:
+                val = float(ln.split(":", 1)[1].strip())
+            except ValueError:
+                val = None
+    return val if (got_sha == sha and val) else None
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def build_sim(pic, I, wl, stream, tuning=None):
+    g = wl["grid"]
+    h = pic.pic_create(pic.make_grid(g["dims"], g["n"], g["d"], g["dt"], bc=g["bc"],
+                                     pml_cells=g["pml_cells"], src=g.get("src")), stream)
+    if tuning:
+        pic.pic_set_tuning(h, **tuning)
+    if wl["mask"] is not None:
+        pic.pic_set_material_mask(h, wl["mask"])
+    for sp in wl["species"]:
+        desc = pic.species_desc(sp["kind"], sp["q"], sp["m"], 0.0, omega0=sp.get("omega0", (0, 0, 0)),
+                                gamma=sp.get("gamma", (0, 0, 0)), v_F=sp.get("v_F", 0.0),
+                                background=sp["background"])
+        pic.pic_load_species(h, desc, density=sp["density"], E_F=sp["E_F"], T=sp["T"],
+                             ppc=sp["ppc"], quiet=sp["quiet"], seed=sp["seed"], stream=sp["stream"])
+    return h
+
+
+def run_gpu(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_07465_gb300 import inputs as I
+    from paper_2501_07465_gb300 import pic
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pic.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    wl = I.sphere3d(n=args.grid, radius_nm=20.0 * args.grid / 256)
+    h = build_sim(pic, I, wl, stream.cuda_stream, tuning=dict(timing=1))
+    diag0 = pic.pic_diagnostics(h)
+    nparts = sum(diag0["count"])
+    nfree, nbound = diag0["count"][0], diag0["count"][1]
+    nmat = int(wl["mask"].sum())
+
+    pic.pic_step(h, args.warmup)
+    pic.pic_sync(h)
+    pic.pic_get_timing(h)  # discard warm-up timings
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                      if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None) as clk:
+        ev0.record(stream)
+        pic.pic_step(h, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    tm = pic.pic_get_timing(h)
+    pic.pic_sync(h)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    total_particles = nparts * world
+    value = total_particles * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel
+    fb, jcells = field_bytes(wl)
+    pb = particle_bytes(nfree, nbound, nmat)
+    f_avg = tm["field_ms"] / max(tm["field_launches"], 1)
+    p_avg = tm["particle_ms"] / max(tm["particle_launches"], 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernels = {
+        "field": dict(bytes=fb, ms=f_avg, src="k_field.cu"),
+        "particle": dict(bytes=pb, ms=p_avg, src="k_particle.cu"),
+    }
+    dom = "field" if tm["field_ms"] >= tm["particle_ms"] else "particle"
+    kd = kernels[dom]
+    achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
+    traffic = traffic_from_profile(f"{dom}_kernel",
+                                   os.path.join(ROOT, "paper_2501_07465_gb300", "csrc", kd["src"]))
+    other = "particle" if dom == "field" else "field"
+    ko = kernels[other]
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(pic, I, wl, h, stream, nparts)
+    fp64 = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, fp64 = cpu_baseline_and_error(pic, I, wl, stream)
+    pic.pic_destroy(h)
+
+    launches_per_step = tm["kernel_launches"] / max(args.steps, 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "grid": list(wl["grid"]["n"]),
+                   "particles_per_gpu": nparts, "free": nfree, "bound": nbound,
+                   "cells": int(np.prod(wl["grid"]["n"])), "material_cells": nmat,
+                   "sort_interval": 32, "l2": "inputs larger than L2 (fields 805 MB, no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": f"{dom}_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} hbm_gbs", "bytes_per_launch": kd["bytes"],
+                     "ms_per_launch": kd["ms"],
+                     "other": {"kernel": f"{other}_kernel", "bytes_per_launch": ko["bytes"],
+                               "ms_per_launch": ko["ms"],
+                               "achieved": ko["bytes"] / (ko["ms"] / 1e3) / 1e9},
+                     "share": {"field": tm["field_ms"], "particle": tm["particle_ms"],
+                               "sort": tm["sort_ms"]}},
+        "bytes_per_particle_step": (fb + pb) / nparts,
+        "step_roofline_frac": (fb + pb) * args.steps / (ms / 1e3) / 1e9 / peak,
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_error": fp64,
+        "clocks": clk.summary(), "gpu_launches": int(tm["kernel_launches"]),
+        "gpu_launches_per_step": launches_per_step,
+    }
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(pic, I, wl, h_ref, stream, nparts):
+    """Whole job through the public API with host buffers: the particle state
+    (pinned host arrays) and the mask go in, the step runs, the diagnostics
+    and the fields come back.  Timed on the host clock with the copies
+    inside; value = particle-steps / job time."""
+    import torch
+    steps = 200
+    g = wl["grid"]
+    hosts = []
+    for k, sp in enumerate(wl["species"]):
+        n = pic.pic_diagnostics(h_ref)["count"][k]
+        rd = pic.pic_read_species(h_ref, k, n, bound=sp["kind"] == I.BOUND)
+        pinned = {}
+        for key, arr in rd.items():
+            t = torch.empty(arr.shape, dtype={np.dtype(np.int32): torch.int32,
+                                              np.dtype(np.float32): torch.float32,
+                                              np.dtype(np.float64): torch.float64}[arr.dtype],
+                            pin_memory=True)
+            t.numpy()[...] = arr
+            pinned[key] = t
+        hosts.append(pinned)
+    mask = torch.from_numpy(wl["mask"]).pin_memory()
+    ncell = int(np.prod(g["n"]))
+    out = torch.empty((6 * ncell,), dtype=torch.float64, pin_memory=True)
+    h2d = mask.numel()
+    for pdict in hosts:
+        h2d += sum(t.numel() * t.element_size() for t in pdict.values())
+    d2h = out.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = pic.pic_create(pic.make_grid(g["dims"], g["n"], g["d"], g["dt"], bc=g["bc"],
+                                     pml_cells=g["pml_cells"], src=g.get("src")),
+                       stream.cuda_stream)
+    pic.pic_set_material_mask(h, mask.numpy())
+    for sp, pdict in zip(wl["species"], hosts):
+        w = sp["density"] * float(np.prod(g["d"])) / sp["ppc"]
+        desc = pic.species_desc(sp["kind"], sp["q"], sp["m"], w, omega0=sp.get("omega0", (0, 0, 0)),
+                                gamma=sp.get("gamma", (0, 0, 0)), v_F=sp.get("v_F", 0.0),
+                                background=sp["background"])
+        pic.pic_load_species(h, desc, cell=pdict["cell"].numpy(),
+                             off=pdict["off"].numpy() if "off" in pdict else None,
+                             v=pdict["v"].numpy(),
+                             anchor_off=pdict["anchor_off"].numpy() if "anchor_off" in pdict else None,
+                             disp=pdict["disp"].numpy() if "disp" in pdict else None,
+                             density=sp["density"])
+    pic.pic_step(h, steps)
+    diag = pic.pic_diagnostics(h)
+    out.numpy()[...] = pic.pic_read_fields(h, 63, (g["n"][2], g["n"][1], g["n"][0])).ravel()
+    t1 = time.perf_counter()
+    pic.pic_destroy(h)
+    return {"value": nparts * steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": (d2h + 512) / steps, "steps": steps,
+            "job": "create + mask + explicit particles from pinned host memory + steps + "
+                   "diagnostics + E/B read back (FP64)", "kinetic0": diag["kinetic"][0]}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle) and the FP32-vs-FP64 error
+# ---------------------------------------------------------------------------
+
+def oracle_setup(I, wl):
+    from oracle import oracle as O
+    g = dict(wl["grid"])
+    src = g.pop("src", None)
+    if src:
+        g.update(src=True, **src)
+    s = O.OracleSim(**g)
+    n = tuple(wl["grid"]["n"])
+    if wl["mask"] is not None:
+        s.set_mask(wl["mask"])
+    for sp in wl["species"]:
+        cell, off, v = O.fd_load(wl["grid"]["dims"], n, wl["mask"], sp["kind"], sp["m"], sp["E_F"],
+                                 sp["T"], sp.get("v_F", 0.0), sp["ppc"], sp["quiet"], sp["seed"],
+                                 sp["stream"])
+        w = sp["density"] * float(np.prod(wl["grid"]["d"])) / sp["ppc"]
+        X = I.cell_coords(cell, n) + off
+        s.add_species(sp["kind"], sp["q"], sp["m"], w, X, v,
+                      D=np.zeros_like(X) if sp["kind"] == I.BOUND else None,
+                      omega0=sp.get("omega0", (0, 0, 0)), gamma=sp.get("gamma", (0, 0, 0)),
+                      vF=sp.get("v_F", 0.0), bg=0)
+    return s
+
+
+CPU_SAMPLE_STEPS = 2
+
+
+def cpu_baseline_and_error(pic, I, wl_full, stream):
+    """Time the oracle on one host core on the half-scale copy of the
+    workload (128^3 cells, sphere radius 10 nm: the same particle-to-cell
+    ratio, 1/8 of the work per step), CPU_SAMPLE_STEPS steps; compare the
+    GPU's run of the same sample (fresh sim, same seeds) with it."""
+    n = wl_full["grid"]["n"][0] // 2
+    wl = I.sphere3d(n=n, radius_nm=20.0 * n / 256)
+    t0 = time.perf_counter()
+    s = oracle_setup(I, wl)
+    t_setup = time.perf_counter() - t0
+    nparts = sum(s.species(k)[0].shape[0] for k in range(s.nsp))
+    t0 = time.perf_counter()
+    s.step(CPU_SAMPLE_STEPS)
+    t_step = (time.perf_counter() - t0) / CPU_SAMPLE_STEPS
+    cpu = {"value": nparts / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{wl['name']}: {CPU_SAMPLE_STEPS} steps ({nparts} particles) after the "
+                     f"oracle's own FD load ({t_setup:.1f} s, not timed); single-threaded FP64 C",
+           "seconds_per_step": t_step}
+    err = None
+    try:
+        h = build_sim(pic, I, wl, stream.cuda_stream)
+        pic.pic_step(h, CPU_SAMPLE_STEPS)
+        g = wl["grid"]
+        shape = (g["n"][2], g["n"][1], g["n"][0])
+        E = pic.pic_read_fields(h, 7, shape)
+        Eo = np.stack([s.field(c) for c in range(3)])
+        vmax = 0.0
+        for k in range(s.nsp):
+            Xo, Vo, _, _ = s.species(k)
+            rd = pic.pic_read_species(h, k, Xo.shape[0], bound=wl["species"][k]["kind"] == I.BOUND)
+            scale = np.maximum(np.linalg.norm(Vo, axis=1), 1e3)
+            vmax = max(vmax, float(np.max(np.linalg.norm(rd["v"] - Vo, axis=1) / scale)))
+        err = {"steps": CPU_SAMPLE_STEPS, "workload": wl["name"], "v_rel_max": vmax,
+               "E_rel_l2": float(np.linalg.norm(E - Eo) / max(np.linalg.norm(Eo), 1e-300))}
+        pic.pic_destroy(h)
+    except Exception as e:  # the error report must not hide the throughput line
+        err = {"error": str(e)[:200]}
+    s.close()
+    return cpu, err
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_2501_07465_gb300 import inputs as I
+    from oracle import oracle as O
+    O.build()
+    # bounded sample: the half-scale copy of the workload (same particle-to-
+    # cell ratio), at most 3 oracle steps
+    n = args.grid // 2
+    wl = I.sphere3d(n=n, radius_nm=20.0 * n / 256)
+    s = oracle_setup(I, wl)
+    nparts = sum(s.species(k)[0].shape[0] for k in range(s.nsp))
+    steps = max(1, min(args.steps, 3))
+    warm = max(0, min(args.warmup, 1))
+    s.step(warm)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    v = nparts * steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "grid": list(wl["grid"]["n"]),
+                   "particles": nparts, "parallelism": "1 host core"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} steps of {wl['name']}, the half-scale copy of "
+                                   f"the GPU workload (requested {args.steps}, capped at 3)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

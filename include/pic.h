@@ -163,8 +163,9 @@ typedef struct pic_diag {
 
 /* Kernel timing totals since the last query (pic_tuning.timing = 1). */
 typedef struct pic_timing {
-    double particle_ms, field_ms, sort_ms;
-    int64_t particle_launches, field_launches, sort_launches;
+    double particle_ms, field_ms, sort_ms;       /* summed CUDA-event durations */
+    int64_t particle_launches, field_launches, sort_launches;  /* timed phases */
+    int64_t kernel_launches;                     /* all kernels pic_step launched */
 } pic_timing;
 
 /* Device memory hooks.  alloc returns a device pointer of `bytes` usable on

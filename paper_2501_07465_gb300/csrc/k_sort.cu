@@ -181,6 +181,12 @@ long long scan_tmp_len(long long n) {
     return nb + (nb + 1) + scan_tmp_len(nb);
 }
 
+int scan_kernel_count(long long n) {
+    if (n <= 0) return 0;
+    long long nb = (n + kScanChunk - 1) / kScanChunk;
+    return nb == 1 ? 1 : 2 + scan_kernel_count(nb);
+}
+
 // Exclusive scan of n ints: out[0..n] (out[n] = total).  tmp: scan_tmp_len(n).
 cudaError_t launch_scan_int(const int *in, int *out_excl, long long n, int *tmp, long long tmp_len,
                             cudaStream_t s) {

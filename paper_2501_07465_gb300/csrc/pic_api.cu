@@ -87,6 +87,7 @@ struct pic_sim {
     double omega_p2 = 0.0, omega_b2 = 0.0;
     std::string err;
     TimedEvents ev[3];  // particle, field, sort
+    long long launches = 0;  // kernels launched by pic_step since the last timing query
 };
 
 namespace {
@@ -252,6 +253,7 @@ pic_status sort_species(pic_sim *s, int i) {
     CK(s, launch_scan_int(s->sort_count, sp.tile_start, tp.ntiles, s->scan_tmp, 0, s->stream));
     CK(s, launch_tile_scatter(s->g, tp, src, sp.pid[sp.cur], dst, sp.pid[1 - sp.cur],
                               sp.tile_start, s->sort_rank, s->stream));
+    s->launches += 2 + scan_kernel_count(tp.ntiles);
     sp.cur = 1 - sp.cur;
     return PIC_OK;
 }
@@ -757,6 +759,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             // tile_start pointers do not move between sorts: starts_dev stays valid
             CK(s, launch_active_tiles_work(s->tp, s->starts_dev, s->nsp, s->active, s->nactive,
                                            s->tile_work, s->stream));
+            s->launches += 2 + scan_kernel_count(s->tp.ntiles);
             record(s, 2, false);
         }
         if (s->tun.keep_J)
@@ -769,6 +772,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
         record(s, 1, true);
         CK(s, launch_field(s->g, f, s->stream));
         record(s, 1, false);
+        s->launches += 2;
         s->fcur ^= 1;
         s->steps++;
         s->since_sort++;
@@ -942,6 +946,8 @@ pic_status pic_get_timing(pic_sim *s, pic_timing *out) {
     out->particle_launches = cnt[0];
     out->field_launches = cnt[1];
     out->sort_launches = cnt[2];
+    out->kernel_launches = s->launches;
+    s->launches = 0;
     return PIC_OK;
 }
 

@@ -131,6 +131,7 @@ cudaError_t launch_tile_histogram(const GridP &g, const TileP &tp, const uint32_
 cudaError_t launch_scan_int(const int *in, int *out_excl, long long n, int *tmp,
                             long long tmp_len, cudaStream_t s);
 long long scan_tmp_len(long long n);
+int scan_kernel_count(long long n);
 cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
                                 const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
                                 const int *start, const int *rank, cudaStream_t s);

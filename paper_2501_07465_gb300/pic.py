@@ -75,7 +75,7 @@ class pic_diag(C.Structure):
 class pic_timing(C.Structure):
     _fields_ = [("particle_ms", C.c_double), ("field_ms", C.c_double), ("sort_ms", C.c_double),
                 ("particle_launches", C.c_int64), ("field_launches", C.c_int64),
-                ("sort_launches", C.c_int64)]
+                ("sort_launches", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -312,7 +312,7 @@ def pic_get_timing(h):
     _check(load_library().pic_get_timing(h, C.byref(t)), h)
     return {"particle_ms": t.particle_ms, "field_ms": t.field_ms, "sort_ms": t.sort_ms,
             "particle_launches": t.particle_launches, "field_launches": t.field_launches,
-            "sort_launches": t.sort_launches}
+            "sort_launches": t.sort_launches, "kernel_launches": t.kernel_launches}
 
 
 def pic_memory_bytes(h):
