@@ -230,6 +230,29 @@ pic_status pic_memory_bytes(const pic_sim *sim, size_t *bytes);
 /* Text of the last error on this handle (never NULL). */
 const char *pic_last_error(const pic_sim *sim);
 
+/* Largest grid (cells) pic_cell_counts_noalloc accepts: 2^22 cells, i.e. a
+   16 MiB int32 array built into the library. */
+#define PIC_NOALLOC_MAX_CELLS (1 << 22)
+
+/* pic_cell_counts without any device allocation.  (No counterpart in the
+   paper: this is a service of the library.)
+   pic_cell_counts asks for a temporary device buffer on every call.  Some
+   callers cannot allow that: code that records work into a CUDA graph (a
+   cudaMalloc cannot be captured), hosts that hand all device memory to a
+   fixed pool or another framework up front, and serving loops where
+   cudaMalloc / cudaFree would synchronise the device and stall other work.
+   This variant counts into a fixed device array of PIC_NOALLOC_MAX_CELLS
+   int32 that lives in the library itself; every device that has loaded the
+   library's code for this call keeps those 16 MiB until the process exits.
+   Arguments and output are those of pic_cell_counts; grids larger than
+   PIC_NOALLOC_MAX_CELLS cells are rejected with PIC_EINVAL.  The first call
+   on a device looks up the array's device address (cudaGetSymbolAddress);
+   make that first call before any stream capture.  All calls share the one
+   array and clear it at the start: calls that run at the same time on the
+   GPU (several streams or threads) race and must be serialised by the
+   caller.  Synchronous: it waits for the simulation's stream. */
+pic_status pic_cell_counts_noalloc(pic_sim *sim, int species, int32_t *host_out, size_t n);
+
 #ifdef __cplusplus
 }
 #endif

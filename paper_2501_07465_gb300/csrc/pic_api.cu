@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -958,3 +959,50 @@ pic_status pic_memory_bytes(const pic_sim *s, size_t *bytes) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Per-cell counts that allocate nothing (pic_cell_counts_noalloc)
+// ---------------------------------------------------------------------------
+
+// The counts live in this fixed array instead of a per-call buffer.  In host
+// code the name only stands for the array; the kernel gets the device address
+// obtained once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) int g_noalloc_counts[PIC_NOALLOC_MAX_CELLS];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+int *g_noalloc_ptr[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" pic_status pic_cell_counts_noalloc(pic_sim *s, int k, int32_t *out, size_t n) {
+    if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
+    if (k < 0 || k >= s->nsp) return fail(s, PIC_EINVAL, "no such species");
+    if ((long long)n != s->g.ncell) return fail(s, PIC_EINVAL, "n must equal the cell count");
+    if (n > (size_t)PIC_NOALLOC_MAX_CELLS)
+        return fail(s, PIC_EINVAL,
+                    "grid has " + std::to_string(n) + " cells; pic_cell_counts_noalloc holds at most " +
+                        std::to_string(PIC_NOALLOC_MAX_CELLS) + " (use pic_cell_counts)");
+    int dev = 0;
+    CK(s, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(s, PIC_EINVAL, "device index too large");
+    int *counts = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_counts);
+            if (e != cudaSuccess || !p)
+                return fail(s, PIC_ECUDA,
+                            std::string("cudaGetSymbolAddress(counts): ") + cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (int *)p;
+        }
+        counts = g_noalloc_ptr[dev];
+    }
+    Species &sp = s->sp[k];
+    CK(s, cudaMemsetAsync(counts, 0, n * sizeof(int), s->stream));
+    CK(s, launch_cell_histogram(s->g, species_params(s, sp, sp.cur), counts, s->stream));
+    CK(s, cudaMemcpyAsync(out, counts, n * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return check_device_status(s);
+}

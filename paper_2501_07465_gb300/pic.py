@@ -103,7 +103,9 @@ SIGNATURES = {
     "pic_get_timing": (C.c_int, [_H, C.POINTER(pic_timing)]),
     "pic_memory_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "pic_last_error": (C.c_char_p, [_H]),
+    "pic_cell_counts_noalloc": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int32), C.c_size_t]),
 }
+PIC_NOALLOC_MAX_CELLS = 1 << 22
 
 _lib = None
 
@@ -294,6 +296,14 @@ def pic_read_species(h, k, n, bound=False):
 def pic_cell_counts(h, k, shape):
     out = np.zeros(tuple(shape), np.int32)
     _check(load_library().pic_cell_counts(h, k, _ptr(out, C.c_int32), out.size), h)
+    return out
+
+
+def pic_cell_counts_noalloc(h, k, shape):
+    """pic_cell_counts without device allocation (fixed in-library array of
+    PIC_NOALLOC_MAX_CELLS cells; larger grids raise PicError)."""
+    out = np.zeros(tuple(shape), np.int32)
+    _check(load_library().pic_cell_counts_noalloc(h, k, _ptr(out, C.c_int32), out.size), h)
     return out
 
 
