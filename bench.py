@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="cells per side (256 = the workload)")
+    ap.add_argument("--tile", type=str, default="", help="particle tile, e.g. 8,8,4")
+    ap.add_argument("--sort-interval", type=int, default=0)
     return ap.parse_args()
 
 
@@ -77,6 +79,13 @@ class ClockSampler:
                 stdout=self.fh, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # nvidia-smi's start-up takes driver locks that stall kernel launches:
+        # let it settle (first sample written) before the timed region opens
+        if self.proc is not None and self.path:
+            t0 = time.time()
+            while time.time() - t0 < 10 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
+            time.sleep(0.3)
         return self
 
     def __exit__(self, *a):
@@ -216,7 +225,12 @@ def run_gpu(args):
     pic.use_torch_allocator()
     stream = torch.cuda.current_stream()
     wl = I.sphere3d(n=args.grid, radius_nm=20.0 * args.grid / 256)
-    h = build_sim(pic, I, wl, stream.cuda_stream, tuning=dict(timing=1))
+    tuning = dict(timing=1)
+    if args.tile:
+        tuning["tile"] = tuple(int(x) for x in args.tile.split(","))
+    if args.sort_interval:
+        tuning["sort_interval"] = args.sort_interval
+    h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning)
     diag0 = pic.pic_diagnostics(h)
     nparts = sum(diag0["count"])
     nfree, nbound = diag0["count"][0], diag0["count"][1]
@@ -257,14 +271,16 @@ def run_gpu(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    tma = wl["grid"]["n"][0] % 4 == 0  # the library feeds the field kernel by TMA then
     kernels = {
-        "field": dict(bytes=fb, ms=f_avg, src="k_field.cu"),
-        "particle": dict(bytes=pb, ms=p_avg, src="k_particle.cu"),
+        "field": dict(bytes=fb, ms=f_avg, src="k_field_tma.cu" if tma else "k_field.cu",
+                      name="field_kernel_tma" if tma else "field_kernel"),
+        "particle": dict(bytes=pb, ms=p_avg, src="k_particle.cu", name="particle_kernel"),
     }
     dom = "field" if tm["field_ms"] >= tm["particle_ms"] else "particle"
     kd = kernels[dom]
     achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
-    traffic = traffic_from_profile(f"{dom}_kernel",
+    traffic = traffic_from_profile(kd["name"],
                                    os.path.join(ROOT, "paper_2501_07465_gb300", "csrc", kd["src"]))
     other = "particle" if dom == "field" else "field"
     ko = kernels[other]
@@ -286,13 +302,14 @@ def run_gpu(args):
         "config": {"workload": wl["name"], "grid": list(wl["grid"]["n"]),
                    "particles_per_gpu": nparts, "free": nfree, "bound": nbound,
                    "cells": int(np.prod(wl["grid"]["n"])), "material_cells": nmat,
-                   "sort_interval": 32, "l2": "inputs larger than L2 (fields 805 MB, no flush)",
+                   "sort_interval": args.sort_interval or 32, "tile": args.tile or "8,8,8",
+                   "l2": "inputs larger than L2 (fields 805 MB, no flush)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": f"{dom}_kernel", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": kd["name"], "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} hbm_gbs", "bytes_per_launch": kd["bytes"],
                      "ms_per_launch": kd["ms"],
-                     "other": {"kernel": f"{other}_kernel", "bytes_per_launch": ko["bytes"],
+                     "other": {"kernel": ko["name"], "bytes_per_launch": ko["bytes"],
                                "ms_per_launch": ko["ms"],
                                "achieved": ko["bytes"] / (ko["ms"] / 1e3) / 1e9},
                      "share": {"field": tm["field_ms"], "particle": tm["particle_ms"],

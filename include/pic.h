@@ -138,12 +138,13 @@ typedef struct pic_particles {
 
 /* Tuning of one simulation (defaults in brackets; 0 keeps the default). */
 typedef struct pic_tuning {
-    int tile[3];        /* particle tile, cells [8,8,8 in 3D; 32,32,1 in 2D] */
+    int tile[3];        /* particle tile, cells [8,8,4 in 3D; 32,32,1 in 2D] */
     int sort_interval;  /* steps between tile re-sorts [32] */
     int field_zchunk;   /* z planes per field-kernel CTA [16] */
     int particle_ctas;  /* persistent particle CTAs [SMs x occupancy] */
     int keep_J;         /* 1: J of the last step stays readable (tests) [0] */
     int timing;         /* 1: time every kernel launch with CUDA events [0] */
+    int field_plain;    /* 1: field kernel with plain loads even where TMA applies [0] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */

@@ -176,6 +176,7 @@ __global__ void fd_particles_kernel(GridP g, FDRequest r, const int *mat_cells, 
         if (r.kind == PIC_BOUND) {
             for (int a = 0; a < 3; ++a) {
                 const_cast<double *>(out.anchor[a])[id] = off[a];
+                const_cast<float *>(out.anchor32[a])[id] = below_one(off[a]);
                 out.disp[a][id] = 0.f;
                 out.v[a][id] = 0.f;
             }

@@ -195,6 +195,10 @@ __device__ inline void shape3(int c0, float f0, int c1, float f1, int lo, float 
 }
 
 template <int DIM, class Acc>
+__device__ inline void deposit_w(const Acc &A, const int *lo, const float (*S0)[3],
+                                 const float (*DS)[3], const float *jf, float vz);
+
+template <int DIM, class Acc>
 __device__ inline void deposit(const Acc &A, const int *c0, const float *f0, const int *c1,
                                const float *f1, const float *jf, float vz) {
     float S0[3][3], DS[3][3];
@@ -203,6 +207,14 @@ __device__ inline void deposit(const Acc &A, const int *c0, const float *f0, con
         lo[a] = min(c0[a], c1[a]);
         shape3(c0[a], f0[a], c1[a], f1[a], lo[a], S0[a], DS[a]);
     }
+    deposit_w<DIM>(A, lo, S0, DS, jf, vz);
+}
+
+// Esirkepov sums for given node bases lo, start shapes S0 and shape changes DS
+// on the three nodes lo .. lo+2 of each axis.
+template <int DIM, class Acc>
+__device__ inline void deposit_w(const Acc &A, const int *lo, const float (*S0)[3],
+                                 const float (*DS)[3], const float *jf, float vz) {
     const float third = 1.0f / 3.0f;
     if (DIM == 3) {
 #pragma unroll
@@ -338,6 +350,77 @@ __device__ inline void dirac_push(float *v, const float *E, const float *B, cons
 }
 
 // ---------------------------------------------------------------------------
+// Esirkepov deposit for a move that stays in its cell (the common case)
+// ---------------------------------------------------------------------------
+
+// With S0 = (1 - f0, f0) and DS = (-dF, dF) on the two nodes of each axis,
+// Esirkepov's transverse factor S0y S0z + (DSy S0z + S0y DSz)/2 +
+// DSy DSz/3 equals my mz + DSy DSz / 12, where m = S0 + DS/2 holds the
+// midpoint weights (1 - fm, fm), fm = f0 + dF/2.  Only the first node of the
+// move axis receives current.
+template <int DIM, class Acc>
+__device__ inline void deposit_nocross(const Acc &A, const int *c, const float *f0, const float *dF,
+                                       const float *jf, float vz) {
+    const float k12 = 1.0f / 12.0f;
+    float m0[2], m1[2], m2[2] = {1.f, 0.f};
+    {
+        float fm = f0[0] + 0.5f * dF[0];
+        m0[0] = 1.f - fm;
+        m0[1] = fm;
+        fm = f0[1] + 0.5f * dF[1];
+        m1[0] = 1.f - fm;
+        m1[1] = fm;
+        if (DIM == 3) {
+            fm = f0[2] + 0.5f * dF[2];
+            m2[0] = 1.f - fm;
+            m2[1] = fm;
+        }
+    }
+    if (DIM == 3) {
+        if (dF[0] != 0.f) {
+            const float cx = -jf[0] * dF[0], e = dF[1] * dF[2] * k12;
+            A.add(0, c[0], c[1], c[2], cx * (m1[0] * m2[0] + e));
+            A.add(0, c[0], c[1], c[2] + 1, cx * (m1[0] * m2[1] - e));
+            A.add(0, c[0], c[1] + 1, c[2], cx * (m1[1] * m2[0] - e));
+            A.add(0, c[0], c[1] + 1, c[2] + 1, cx * (m1[1] * m2[1] + e));
+        }
+        if (dF[1] != 0.f) {
+            const float cy = -jf[1] * dF[1], e = dF[0] * dF[2] * k12;
+            A.add(1, c[0], c[1], c[2], cy * (m0[0] * m2[0] + e));
+            A.add(1, c[0], c[1], c[2] + 1, cy * (m0[0] * m2[1] - e));
+            A.add(1, c[0] + 1, c[1], c[2], cy * (m0[1] * m2[0] - e));
+            A.add(1, c[0] + 1, c[1], c[2] + 1, cy * (m0[1] * m2[1] + e));
+        }
+        if (dF[2] != 0.f) {
+            const float cz = -jf[2] * dF[2], e = dF[0] * dF[1] * k12;
+            A.add(2, c[0], c[1], c[2], cz * (m0[0] * m1[0] + e));
+            A.add(2, c[0], c[1] + 1, c[2], cz * (m0[0] * m1[1] - e));
+            A.add(2, c[0] + 1, c[1], c[2], cz * (m0[1] * m1[0] - e));
+            A.add(2, c[0] + 1, c[1] + 1, c[2], cz * (m0[1] * m1[1] + e));
+        }
+    } else {
+        if (dF[0] != 0.f) {
+            const float cx = -jf[0] * dF[0];
+            A.add(0, c[0], c[1], 0, cx * m1[0]);
+            A.add(0, c[0], c[1] + 1, 0, cx * m1[1]);
+        }
+        if (dF[1] != 0.f) {
+            const float cy = -jf[1] * dF[1];
+            A.add(1, c[0], c[1], 0, cy * m0[0]);
+            A.add(1, c[0] + 1, c[1], 0, cy * m0[1]);
+        }
+        const float fz = jf[2] * vz;
+        if (fz != 0.f) {
+            const float e = dF[0] * dF[1] * k12;
+            A.add(2, c[0], c[1], 0, fz * (m0[0] * m1[0] + e));
+            A.add(2, c[0], c[1] + 1, 0, fz * (m0[0] * m1[1] - e));
+            A.add(2, c[0] + 1, c[1], 0, fz * (m0[1] * m1[0] - e));
+            A.add(2, c[0] + 1, c[1] + 1, 0, fz * (m0[1] * m1[1] + e));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // one particle
 // ---------------------------------------------------------------------------
 
@@ -352,97 +435,53 @@ __device__ inline int mask_at(const ParticleLaunch &P, int x, int y, int z, bool
     return __ldg(P.mask + ((long long)gz * g.n[1] + gy) * g.n[0] + gx) != 0;
 }
 
-// Process particle p of species s.  org = tile origin (global cell), box
-// accessor for the fast path, global accessor for the slow path.
+// local cell of a particle relative to the tile origin, unwrapped across
+// periodic edges (so that a particle that drifted over the edge stays near
+// its tile)
 template <int DIM>
-__device__ inline unsigned process_particle(const ParticleLaunch &P, const SpeciesP &s, long long p,
-                                            const int *org, const BoxAcc &box,
-                                            const GlobalAcc<DIM> &glob) {
-    const GridP &g = P.g;
-    const uint32_t pc = s.cell[p];
-    const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
-    // local cell relative to the tile origin, unwrapped across periodic edges
-    int lc[3];
+__device__ inline void local_cell(const ParticleLaunch &P, const int *gc, const int *org, int *lc) {
     for (int a = 0; a < 3; ++a) {
         int l = gc[a] - org[a];
-        if (a < DIM && g.per[a]) {
-            int n = g.n[a];
+        if (a < DIM && P.g.per[a]) {
+            const int n = P.g.n[a];
             if (l < -kHalo) l += n;
             else if (l > P.tp.T[a] + kHalo) l -= n;
         }
         lc[a] = a < DIM ? l : 0;
     }
+}
+
+template <int DIM>
+__device__ inline bool in_core(const ParticleLaunch &P, const int *c) {
+    bool ok = true;
+    for (int a = 0; a < DIM; ++a) ok = ok && c[a] >= -1 && c[a] <= P.tp.T[a];
+    return ok;
+}
+
+// Free electrons and Dirac carriers.
+template <int DIM, int KIND>
+__device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &s, long long p,
+                                       const int *org, const BoxAcc &box,
+                                       const GlobalAcc<DIM> &glob) {
+    const GridP &g = P.g;
+    const uint32_t pc = s.cell[p];
+    const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
+    int lc[3];
+    local_cell<DIM>(P, gc, org, lc);
     float v[3] = {s.v[0][p], s.v[1][p], s.v[2][p]};
-    float E[3], B[3];
-    unsigned refl = 0;
-
-    if (s.kind == PIC_BOUND) {
-        // position = anchor cell + anchor offset (FP64) + displacement / d
-        float D[3] = {s.disp[0][p], s.disp[1][p], s.disp[2][p]};
-        int c0[3], c1[3];
-        float f0[3], f1[3];
-        double an[3];
-        for (int a = 0; a < 3; ++a) {
-            an[a] = (a < DIM) ? s.anchor[a][p] : 0.5;
-            double X = an[a] + (double)D[a] * (double)g.inv_d[a];
-            double fl = floor(X);
-            c0[a] = lc[a] + (int)fl;
-            f0[a] = (float)(X - fl);
-            if (a >= DIM) { c0[a] = 0; f0[a] = 0.f; }
-        }
-        bool fast = true;
-        for (int a = 0; a < DIM; ++a) fast = fast && c0[a] >= -1 && c0[a] <= P.tp.T[a];
-        if (fast) gather<DIM>(box, c0, f0, E, B);
-        else {
-            int gg[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
-            gather<DIM>(glob, gg, f0, E, B);
-        }
-        bound_push(v, D, E, B, s);
-        bool jump = false;
-        for (int a = 0; a < 3; ++a) {
-            double X = an[a] + (double)D[a] * (double)g.inv_d[a];
-            double fl = floor(X);
-            c1[a] = lc[a] + (int)fl;
-            f1[a] = clamp_below_one((float)(X - fl));
-            if (a >= DIM) { c1[a] = 0; f1[a] = 0.f; }
-            jump = jump || c1[a] - c0[a] > 1 || c0[a] - c1[a] > 1 || !(X == X);
-        }
-        if (jump) {
-            // more than one cell in one step (or NaN): record, deposit nothing
-            atomicOr(P.status, kStatusBounds);
-            for (int a = 0; a < 3; ++a) { c1[a] = c0[a]; f1[a] = f0[a]; }
-        }
-        if (fast) deposit<DIM>(box, c0, f0, c1, f1, s.jfac, v[2]);
-        else {
-            int g0[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
-            int g1[3] = {c1[0] + org[0], c1[1] + org[1], c1[2] + org[2]};
-            deposit<DIM>(glob, g0, f0, g1, f1, s.jfac, v[2]);
-        }
-        s.disp[0][p] = D[0];
-        s.disp[1][p] = D[1];
-        s.disp[2][p] = D[2];
-        s.v[0][p] = v[0];
-        s.v[1][p] = v[1];
-        s.v[2][p] = v[2];
-        return 0;
-    }
-
     float f0[3] = {s.o[0][p], s.o[1][p], DIM == 3 ? s.o[2][p] : 0.f};
-    bool fast = true;
-    for (int a = 0; a < DIM; ++a) fast = fast && lc[a] >= -1 && lc[a] <= P.tp.T[a];
+    float E[3], B[3];
+    const bool fast = in_core<DIM>(P, lc);
     if (fast) gather<DIM>(box, lc, f0, E, B);
     else gather<DIM>(glob, gc, f0, E, B);
 
-    if (s.kind == PIC_DIRAC) dirac_push(v, E, B, s);
+    if (KIND == PIC_DIRAC) dirac_push(v, E, B, s);
     else boris(v, E, B, s.hq);
 
-    // drift, cell change
-    float f1[3];
+    // drift; at most one cell per axis per step
+    float f1[3] = {f0[0], f0[1], f0[2]};
     int sh[3] = {0, 0, 0};
-    bool moved = false;
-    for (int a = 0; a < 3; ++a) {
-        f1[a] = f0[a];
-        if (a >= DIM) continue;
+    for (int a = 0; a < DIM; ++a) {
         float x = f0[a] + s.dtd[a] * v[a];
         if (!(x > -1.f && x < 2.f)) {
             // more than one cell in one step (or NaN): record and stay put
@@ -452,13 +491,15 @@ __device__ inline unsigned process_particle(const ParticleLaunch &P, const Speci
         if (x >= 1.f) { sh[a] = 1; x -= 1.f; }
         else if (x < 0.f) { sh[a] = -1; x += 1.f; }
         f1[a] = clamp_below_one(x);
-        moved = moved || sh[a] != 0;
     }
+    unsigned refl = 0;
+    const bool moved = (sh[0] | sh[1] | sh[2]) != 0;
     if (moved) {
         bool out1, out0;
         int m1 = mask_at(P, gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2], out1);
         int m0 = mask_at(P, gc[0], gc[1], gc[2], out0);
         if (out1 || (m0 && !m1)) {
+            // specular reflection at the crossed faces (Sec. 3)
             for (int a = 0; a < DIM; ++a) {
                 if (sh[a] == 0) continue;
                 f1[a] = clamp_below_one(1.f - f1[a]);
@@ -468,13 +509,18 @@ __device__ inline unsigned process_particle(const ParticleLaunch &P, const Speci
             refl = 1;
         }
     }
-    int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
-    if (fast) deposit<DIM>(box, lc, f0, c1l, f1, s.jfac, v[2]);
-    else {
-        int g1[3] = {gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2]};
-        deposit<DIM>(glob, gc, f0, g1, f1, s.jfac, v[2]);
-    }
-    if (sh[0] | sh[1] | sh[2]) {
+    if (!(sh[0] | sh[1] | sh[2])) {
+        // stays in its cell: f1 - f0 is exact in FP32 (Sterbenz)
+        const float dF[3] = {f1[0] - f0[0], f1[1] - f0[1], DIM == 3 ? f1[2] - f0[2] : 0.f};
+        if (fast) deposit_nocross<DIM>(box, lc, f0, dF, s.jfac, v[2]);
+        else deposit_nocross<DIM>(glob, gc, f0, dF, s.jfac, v[2]);
+    } else {
+        int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
+        if (fast) deposit<DIM>(box, lc, f0, c1l, f1, s.jfac, v[2]);
+        else {
+            int g1[3] = {gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2]};
+            deposit<DIM>(glob, gc, f0, g1, f1, s.jfac, v[2]);
+        }
         int nxc[3];
         for (int a = 0; a < 3; ++a) {
             nxc[a] = gc[a] + sh[a];
@@ -489,6 +535,97 @@ __device__ inline unsigned process_particle(const ParticleLaunch &P, const Speci
     s.v[1][p] = v[1];
     s.v[2][p] = v[2];
     return refl;
+}
+
+// Bound electrons.  Position = anchor cell + anchor offset + D / d.  The hot
+// loop reads the FP32 copy of the anchor offset (the FP64 anchor is the
+// stored rest position).  The current uses the move dt v / d of this step
+// directly: it is far below an FP32 ulp of the offset, and the displacement D
+// itself is ~100x the per-step move, so differences of stored values would
+// lose most of its bits.
+template <int DIM>
+__device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, long long p,
+                                  const int *org, const BoxAcc &box, const GlobalAcc<DIM> &glob) {
+    const GridP &g = P.g;
+    const uint32_t pc = s.cell[p];
+    const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
+    int lc[3];
+    local_cell<DIM>(P, gc, org, lc);
+    float v[3] = {s.v[0][p], s.v[1][p], s.v[2][p]};
+    float D[3] = {s.disp[0][p], s.disp[1][p], s.disp[2][p]};
+    float an[3];
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+    float f0[3] = {0.f, 0.f, 0.f}, f1[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < DIM; ++a) {
+        an[a] = s.anchor32[a][p];
+        float X = an[a] + D[a] * g.inv_d[a];
+        float fl = floorf(X);
+        c0[a] = lc[a] + (int)fl;
+        f0[a] = clamp_below_one(X - fl);
+    }
+    float E[3], B[3];
+    const bool fast = in_core<DIM>(P, c0);
+    if (fast) gather<DIM>(box, c0, f0, E, B);
+    else {
+        int gg[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
+        gather<DIM>(glob, gg, f0, E, B);
+    }
+    bound_push(v, D, E, B, s);
+    float dF[3] = {0.f, 0.f, 0.f};
+    int sh[3] = {0, 0, 0};
+    bool jump = false;
+    for (int a = 0; a < DIM; ++a) {
+        dF[a] = s.dt * v[a] * g.inv_d[a];
+        const float x = f0[a] + dF[a];
+        sh[a] = x >= 1.f ? 1 : (x < 0.f ? -1 : 0);
+        jump = jump || !(x > -1.f && x < 2.f);
+    }
+    (void)c1;
+    (void)f1;
+    if (jump) {
+        // more than one cell in one step (or NaN): record, deposit nothing
+        atomicOr(P.status, kStatusBounds);
+    } else if (!(sh[0] | sh[1] | sh[2])) {
+        if (fast) deposit_nocross<DIM>(box, c0, f0, dF, s.jfac, v[2]);
+        else {
+            int g0[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
+            deposit_nocross<DIM>(glob, g0, f0, dF, s.jfac, v[2]);
+        }
+    } else {
+        // shapes on the nodes lo .. lo+2 written from (f0, dF) so that the
+        // small move is not rounded against offsets near 1
+        float S0[3][3], DS[3][3];
+        int lo[3];
+        for (int a = 0; a < DIM; ++a) {
+            const float f = f0[a], d = dF[a];
+            if (sh[a] == 0) {
+                lo[a] = c0[a];
+                S0[a][0] = 1.f - f; S0[a][1] = f; S0[a][2] = 0.f;
+                DS[a][0] = -d; DS[a][1] = d; DS[a][2] = 0.f;
+            } else if (sh[a] > 0) {
+                const float e0 = 1.f - f, f1u = d - e0;
+                lo[a] = c0[a];
+                S0[a][0] = e0; S0[a][1] = f; S0[a][2] = 0.f;
+                DS[a][0] = -e0; DS[a][1] = e0 - f1u; DS[a][2] = f1u;
+            } else {
+                const float x = f + d;
+                lo[a] = c0[a] - 1;
+                S0[a][0] = 0.f; S0[a][1] = 1.f - f; S0[a][2] = f;
+                DS[a][0] = -x; DS[a][1] = x + f; DS[a][2] = -f;
+            }
+        }
+        if (fast) deposit_w<DIM>(box, lo, S0, DS, s.jfac, v[2]);
+        else {
+            int g0[3] = {lo[0] + org[0], lo[1] + org[1], lo[2] + org[2]};
+            deposit_w<DIM>(glob, g0, S0, DS, s.jfac, v[2]);
+        }
+    }
+    s.disp[0][p] = D[0];
+    s.disp[1][p] = D[1];
+    s.disp[2][p] = D[2];
+    s.v[0][p] = v[0];
+    s.v[1][p] = v[1];
+    s.v[2][p] = v[2];
 }
 
 // ---------------------------------------------------------------------------
@@ -575,8 +712,15 @@ __global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
             const SpeciesP &s = P.sp[si];
             const long long a = s.tile_start[t], b = s.tile_start[t + 1];
             unsigned r = 0;
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
-                r += process_particle<DIM>(P, s, p, org, box, glob);
+            if (s.kind == PIC_BOUND) {
+                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                    push_bound<DIM>(P, s, p, org, box, glob);
+            } else if (s.kind == PIC_DIRAC) {
+                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                    r += push_mobile<DIM, PIC_DIRAC>(P, s, p, org, box, glob);
+            } else {
+                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                    r += push_mobile<DIM, PIC_FREE>(P, s, p, org, box, glob);
             }
             if (r) atomicAdd(&s_refl[si], r);
         }

@@ -109,13 +109,22 @@ __global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         uint32_t c = src.cell[p];
-        long long d = (long long)start[tile_of(tp, c)] + rank[p];
+        const int t = tile_of(tp, c);
+        // Spread the slots of a tile with a multiplicative permutation so
+        // that consecutive particles (one warp) land in different cells and
+        // their shared-memory current atomics do not collide.
+        const long long cnt = (long long)start[t + 1] - start[t];
+        long long P = 7919;
+        if (cnt % P == 0) P = 7907;
+        if (cnt % P == 0) P = 7901;
+        long long d = (long long)start[t] + ((long long)rank[p] * P) % cnt;
         dst.cell[d] = c;
         pid_dst[d] = pid_src[p];
         for (int a = 0; a < 3; ++a) mv(dst.v[a], src.v[a], d, p);
         if (src.kind == PIC_BOUND) {
             for (int a = 0; a < 3; ++a) {
                 mv(const_cast<double *>(dst.anchor[a]), src.anchor[a], d, p);
+                mv(const_cast<float *>(dst.anchor32[a]), src.anchor32[a], d, p);
                 mv(dst.disp[a], src.disp[a], d, p);
             }
         } else {

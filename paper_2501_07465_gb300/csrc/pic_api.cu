@@ -38,6 +38,7 @@ struct Species {
     float *o[2][3] = {};
     float *v[2][3] = {};
     double *anchor[2][3] = {};
+    float *anchor32[2][3] = {};
     float *disp[2][3] = {};
     int *tile_start = nullptr;
     unsigned long long *nrefl = nullptr;
@@ -89,6 +90,8 @@ struct pic_sim {
     std::string err;
     TimedEvents ev[3];  // particle, field, sort
     long long launches = 0;  // kernels launched by pic_step since the last timing query
+    TmaMaps maps;            // TMA descriptors of the field arrays
+    bool use_tma = false;    // TMA field kernel (needs nx % 4 == 0)
 };
 
 namespace {
@@ -211,6 +214,7 @@ SpeciesP species_params(const pic_sim *s, const Species &sp, int buf) {
         p.o[a] = sp.o[buf][a];
         p.v[a] = sp.v[buf][a];
         p.anchor[a] = sp.anchor[buf][a];
+        p.anchor32[a] = sp.anchor32[buf][a];
         p.disp[a] = sp.disp[buf][a];
         p.hw0sq[a] = (float)(0.5 * dt * d.omega0[a] * d.omega0[a]);
         p.dtd[a] = (float)(dt / dd[a]);
@@ -448,7 +452,7 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
     // default tuning
     s->tun.tile[0] = d.dims == 3 ? 8 : 32;
     s->tun.tile[1] = d.dims == 3 ? 8 : 32;
-    s->tun.tile[2] = d.dims == 3 ? 8 : 1;
+    s->tun.tile[2] = d.dims == 3 ? 4 : 1;
     s->tun.sort_interval = 32;
     s->tun.field_zchunk = 16;
     const long long nc = g.ncell;
@@ -505,6 +509,10 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
         pic_destroy(s);
         return fail(nullptr, st, m);
     }
+    // TMA-fed field kernel where the layout allows it (row pitch a multiple of 16 B)
+    if (encode_field_maps(g, s->E, s->B, s->J, &s->maps) && field_tma_setup() == cudaSuccess)
+        s->use_tma = true;
+    cudaGetLastError();
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
         std::string m = cudaGetErrorString(cudaGetLastError());
         pic_destroy(s);
@@ -549,6 +557,7 @@ pic_status pic_set_tuning(pic_sim *s, const pic_tuning *t) {
     if (t->particle_ctas > 0) nt.particle_ctas = t->particle_ctas;
     nt.keep_J = t->keep_J;
     nt.timing = t->timing;
+    nt.field_plain = t->field_plain;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;
@@ -643,7 +652,8 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
         for (int a = 0; a < 3 && ok; ++a) {
             ok = ok && alloc_zero(s, &sp.v[b][a], na);
             if (d->kind == PIC_BOUND)
-                ok = ok && alloc_zero(s, &sp.anchor[b][a], na) && alloc_zero(s, &sp.disp[b][a], na);
+                ok = ok && alloc_zero(s, &sp.anchor[b][a], na) && alloc_zero(s, &sp.disp[b][a], na) &&
+                     alloc_zero(s, &sp.anchor32[b][a], na);
             else ok = ok && alloc_zero(s, &sp.o[b][a], na);
         }
     }
@@ -702,6 +712,11 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
             if (d->kind == PIC_BOUND) {
                 for (long long p = 0; p < n; ++p) hd[p] = pp->anchor_off[3 * p + a];
                 CK(s, cudaMemcpy(sp.anchor[0][a], hd.data(), n * 8, cudaMemcpyHostToDevice));
+                for (long long p = 0; p < n; ++p) {
+                    float f = (float)hd[p];
+                    hv[p] = f < 1.0f ? f : 0x1.fffffep-1f;
+                }
+                CK(s, cudaMemcpy(sp.anchor32[0][a], hv.data(), n * 4, cudaMemcpyHostToDevice));
                 for (long long p = 0; p < n; ++p) hv[p] = pp->disp ? pp->disp[3 * p + a] : 0.f;
                 CK(s, cudaMemcpy(sp.disp[0][a], hv.data(), n * 4, cudaMemcpyHostToDevice));
             } else {
@@ -771,7 +786,9 @@ pic_status pic_step(pic_sim *s, int nsteps) {
         record(s, 0, false);
         FieldP f = field_params(s);
         record(s, 1, true);
-        CK(s, launch_field(s->g, f, s->stream));
+        if (s->use_tma && !s->tun.field_plain)
+            CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
+        else CK(s, launch_field(s->g, f, s->stream));
         record(s, 1, false);
         s->launches += 2;
         s->fcur ^= 1;

@@ -2,6 +2,8 @@
 // the PIC step.  Shared by the CUDA translation units of libpic.so only.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,7 +48,8 @@ struct SpeciesP {
     uint32_t *cell;               // packed cell (anchor cell for bound)
     float *o[3];                  // in-cell offset (free, Dirac)
     float *v[3];                  // velocity (m/s)
-    const double *anchor[3];      // bound: anchor offset in [0,1), FP64
+    const double *anchor[3];      // bound: anchor offset in [0,1), FP64 (the stored rest position)
+    const float *anchor32[3];     // bound: the same offset rounded to FP32 (read by the step)
     float *disp[3];               // bound: displacement from the anchor (m)
     const int *tile_start;        // [ntiles + 1]
     float hq;                     // q dt / (2 m)
@@ -117,10 +120,23 @@ struct ParticleLaunch {
     int *status;
 };
 
+// TMA descriptors of the field arrays (ping-pong E and B, J)
+struct TmaMaps {
+    CUtensorMap E[2][3];
+    CUtensorMap B[2][3];
+    CUtensorMap J[3];
+};
+
 // ---------------------------------------------------------------------------
 // host-side launch wrappers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
+bool encode_field_maps(const GridP &g, float *const E[2][3], float *const B[2][3],
+                       float *const J[3], TmaMaps *maps);
+cudaError_t field_tma_setup();
+size_t field_tma_smem_bytes();
+cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
+                             int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm);

@@ -58,9 +58,14 @@ def _plane_wave_fields(grid):
 
 @pytest.mark.parametrize("dims,bc,src", [(3, (0, 0, 0), False), (3, (1, 1, 1), True),
                                          (3, (0, 0, 1), True), (2, (1, 0, 0), True),
-                                         (2, (1, 1, 0), False)])
-def test_field_update_matches_oracle(dims, bc, src):
-    n = (45, 20, 36) if dims == 3 else (70, 41, 1)
+                                         (2, (1, 1, 0), False), (2, (0, 0, 0), True)])
+@pytest.mark.parametrize("nx,plain", [(45, 0), (44, 0), (44, 1), (64, 0)])
+def test_field_update_matches_oracle(dims, bc, src, nx, plain):
+    """nx = 44 and 64 take the TMA-fed kernel (row pitch a multiple of 16 B; 44
+    leaves a ragged last block), nx = 45 and plain = 1 the plain-load one."""
+    n = (nx, 20, 36) if dims == 3 else (nx + 25, 41, 1)
+    if dims == 2 and nx % 4 == 0:
+        n = (nx + 24, 41, 1)
     d = (1e-9, 0.8e-9, 1.1e-9)
     dt = 0.45 * min(d[:dims]) / (I.C_LIGHT * math.sqrt(dims))
     grid = dict(dims=dims, n=n, d=d, dt=dt, bc=bc, pml_cells=6)
@@ -70,7 +75,7 @@ def test_field_update_matches_oracle(dims, bc, src):
                            omega=2 * np.pi * I.C_LIGHT / 30e-9, tau=4e-17, t0=6e-17)
     fields = _plane_wave_fields(grid)
     pic = _pic()
-    h = PR.gpu_sim(grid, None, [], fields=fields)
+    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_plain=plain))
     s = PR.oracle_sim(grid, None, [], fields=fields)
     try:
         for nsteps, tol in ((1, 1e-5), (99, 1e-3)):
@@ -109,9 +114,10 @@ def _sphere_case(rng, n=(30, 26, 22), radius=8.0, nfree=6000, nbound=4000, bc=(1
     return grid, mask, species
 
 
-def test_sphere_one_step_particles_fields_counts():
+@pytest.mark.parametrize("n", [(30, 26, 22), (32, 28, 24)])
+def test_sphere_one_step_particles_fields_counts(n):
     rng = np.random.default_rng(11)
-    grid, mask, species = _sphere_case(rng)
+    grid, mask, species = _sphere_case(rng, n=n)
     pic = _pic()
     n = grid["n"]
     s = PR.oracle_sim(grid, mask, species)
@@ -159,9 +165,10 @@ def test_sphere_one_step_particles_fields_counts():
         s.close()
 
 
-def test_sphere_hundred_steps():
+@pytest.mark.parametrize("n", [(30, 26, 22), (36, 26, 22)])
+def test_sphere_hundred_steps(n):
     rng = np.random.default_rng(12)
-    grid, mask, species = _sphere_case(rng, vscale=1.5e6)
+    grid, mask, species = _sphere_case(rng, n=n, vscale=1.5e6)
     pic = _pic()
     n = grid["n"]
     s = PR.oracle_sim(grid, mask, species)
@@ -431,3 +438,32 @@ def test_langmuir_frequency_on_gpu():
         pic.pic_destroy(h)
     wfit = _fit_frequency(np.array(t), np.array(y), wp)
     assert abs(wfit / wp - 1) < 0.01
+
+
+def test_bound_only_current_parity():
+    """The bound current comes from displacements of ~1e-5 cell per step; it
+    must match the oracle's J to 1e-5 even where free electrons are absent."""
+    rng = np.random.default_rng(51)
+    n = (24, 20, 18)
+    d = (0.5e-9,) * 3
+    dt = 0.5 * d[0] / (I.C_LIGHT * math.sqrt(3))
+    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(0, 0, 0))
+    cb, anc, disp, vb = I.random_bound(rng, n, 30000, dscale=3e-12, vscale=3e4)
+    w0 = 2 * np.pi * I.C_LIGHT / 400e-9
+    # the workload's bound density: n_b = 2.95e28 m^-3 over the particles per cell
+    w = 2.95e28 * np.prod(d) * np.prod(n) / cb.size
+    species = [dict(kind=I.BOUND, q=-I.QE, m=I.ME, w=w, cell=cb, anchor_off=anc, disp=disp,
+                    v=vb, omega0=(w0, w0, w0), gamma=(1e14,) * 3)]
+    pic = _pic()
+    s = PR.oracle_sim(grid, None, species)
+    h = PR.gpu_sim(grid, None, species, tuning=dict(keep_J=1))
+    try:
+        for it in range(3):
+            pic.pic_step(h, 1)
+            s.step(1)
+            got = PR.gpu_fields(h, grid, comps=(6, 7, 8))
+            ref = np.stack([s.field(6 + c) for c in range(3)])
+            assert PR.rel_l2(got, ref) < 1e-5, (it, PR.rel_l2(got, ref))
+    finally:
+        pic.pic_destroy(h)
+        s.close()
