@@ -22,6 +22,8 @@
 // flight and ends the CTA.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -149,22 +151,24 @@ __device__ inline float tb(const Stage &s, int c, int lx, int ly) {
     return s.B[c][(ly + 1) * BW + lx + 4];
 }
 
-// B^{n+1/2} at local (lx, ly) of plane k (global gi, gj, k in the domain)
-template <int DIM>
+// B^{n+1/2} at local (lx, ly) of plane k (global gi, gj, k in the domain).
+// PML = false: no cell of the CTA's plane lies in a CPML slab, the memory
+// terms vanish and the plain Yee update is used.
+template <int DIM, bool PML>
 __device__ inline void compute_B(const GridP &g, const FieldP &f, const Stage &cur,
                                  const Stage &nxt, int lx, int ly, int gi, int gj, int k, int comps,
                                  bool write_psi, float *out) {
     const float dt = g.dt;
-    const long long px = psi_index(g, f, 0, gi, gj, k);
-    const long long py = psi_index(g, f, 1, gi, gj, k);
-    const long long pz = DIM == 3 ? psi_index(g, f, 2, gi, gj, k) : -1;
+    const long long px = PML ? psi_index(g, f, 0, gi, gj, k) : -1;
+    const long long py = PML ? psi_index(g, f, 1, gi, gj, k) : -1;
+    const long long pz = (PML && DIM == 3) ? psi_index(g, f, 2, gi, gj, k) : -1;
     if (comps & 1) {  // B_x at (i, j+1/2, k+1/2)
         float dEz_dy = (te(cur, 2, lx, ly + 1) - te(cur, 2, lx, ly)) * g.inv_d[1];
-        float t1 = cpml_term(f, 1, 2, py, gj, true, dEz_dy, write_psi);
+        float t1 = (PML ? cpml_term(f, 1, 2, py, gj, true, dEz_dy, write_psi) : dEz_dy);
         float t2 = 0.f;
         if (DIM == 3) {
             float dEy_dz = (te(nxt, 1, lx, ly) - te(cur, 1, lx, ly)) * g.inv_d[2];
-            t2 = cpml_term(f, 2, 2, pz, k, true, dEy_dz, write_psi);
+            t2 = PML ? cpml_term(f, 2, 2, pz, k, true, dEy_dz, write_psi) : dEy_dz;
         }
         out[0] = tb(cur, 0, lx, ly) - dt * (t1 - t2);
     }
@@ -172,17 +176,17 @@ __device__ inline void compute_B(const GridP &g, const FieldP &f, const Stage &c
         float t1 = 0.f;
         if (DIM == 3) {
             float dEx_dz = (te(nxt, 0, lx, ly) - te(cur, 0, lx, ly)) * g.inv_d[2];
-            t1 = cpml_term(f, 2, 3, pz, k, true, dEx_dz, write_psi);
+            t1 = PML ? cpml_term(f, 2, 3, pz, k, true, dEx_dz, write_psi) : dEx_dz;
         }
         float dEz_dx = (te(cur, 2, lx + 1, ly) - te(cur, 2, lx, ly)) * g.inv_d[0];
-        float t2 = cpml_term(f, 0, 2, px, gi, true, dEz_dx, write_psi);
+        float t2 = PML ? cpml_term(f, 0, 2, px, gi, true, dEz_dx, write_psi) : dEz_dx;
         out[1] = tb(cur, 1, lx, ly) - dt * (t1 - t2);
     }
     if (comps & 4) {  // B_z at (i+1/2, j+1/2, k)
         float dEy_dx = (te(cur, 1, lx + 1, ly) - te(cur, 1, lx, ly)) * g.inv_d[0];
         float dEx_dy = (te(cur, 0, lx, ly + 1) - te(cur, 0, lx, ly)) * g.inv_d[1];
-        float t1 = cpml_term(f, 0, 3, px, gi, true, dEy_dx, write_psi);
-        float t2 = cpml_term(f, 1, 3, py, gj, true, dEx_dy, write_psi);
+        float t1 = PML ? cpml_term(f, 0, 3, px, gi, true, dEy_dx, write_psi) : dEy_dx;
+        float t2 = PML ? cpml_term(f, 1, 3, py, gj, true, dEx_dy, write_psi) : dEx_dy;
         out[2] = tb(cur, 2, lx, ly) - dt * (t1 - t2);
     }
 }
@@ -298,6 +302,12 @@ __global__ void __launch_bounds__(NT, 4)
     const bool halo_valid = (halo_col && j0 + hly < ny && hgi >= 0) ||
                             (halo_row && i0 + hlx < nx && hgj >= 0);
 
+    // CTA-uniform: does any cell this CTA reads or writes lie in a CPML slab?
+    const int P = f.P;
+    const bool xyslab = (f.pml[0] && (i0 - 1 < P || i0 + BX > nx - P)) ||
+                        (f.pml[1] && (j0 - 1 < P || j0 + BY > ny - P));
+    auto zslab = [&](int k) { return DIM == 3 && f.pml[2] && (k < P || k >= nz - P); };
+
     float Bx_prev = 0.f, By_prev = 0.f;
     bool ok = true;
     if (DIM == 3) {
@@ -314,8 +324,8 @@ __global__ void __launch_bounds__(NT, 4)
             const int km1 = zplane(kfirst);
             if (own && km1 >= 0) {
                 float b[3];
-                compute_B<DIM>(g, f, stage_ptrs(smem, slot_of(kfirst)), stage_ptrs(smem, slot_of(k0)),
-                               tx, ty, i, j, km1, 3, false, b);
+                compute_B<DIM, true>(g, f, stage_ptrs(smem, slot_of(kfirst)),
+                                     stage_ptrs(smem, slot_of(k0)), tx, ty, i, j, km1, 3, false, b);
                 Bx_prev = b[0];
                 By_prev = b[1];
             }
@@ -341,24 +351,27 @@ __global__ void __launch_bounds__(NT, 4)
         const Stage sc = stage_ptrs(smem, slot_of(k));
         const Stage sn = DIM == 3 ? stage_ptrs(smem, slot_of(k + 1)) : sc;
         const long long o = ((long long)k * ny + j) * nx + i;
-        float bown[3] = {0.f, 0.f, 0.f};
-        if (own) {
-            compute_B<DIM>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
-            f.Bn[0][o] = bown[0];
-            f.Bn[1][o] = bown[1];
-            f.Bn[2][o] = bown[2];
-        }
-        sB[(0 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[0];
-        sB[(1 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[1];
-        sB[(2 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[2];
-        if (halo_col || halo_row) {
-            float hb[3] = {0.f, 0.f, 0.f};
-            if (halo_valid)
-                compute_B<DIM>(g, f, sc, sn, hlx, hly, hgi, hgj, k, halo_col ? 6 : 5, false, hb);
-            for (int c = 0; c < 3; ++c) sB[(c * (BY + 1) + hly + 1) * (BX + 1) + hlx + 1] = hb[c];
-        }
-        __syncthreads();  // B: sB of plane k complete
-        if (own) {
+        auto plane = [&](auto pml_tag) {
+            constexpr bool PML = decltype(pml_tag)::value;
+            float bown[3] = {0.f, 0.f, 0.f};
+            if (own) {
+                compute_B<DIM, PML>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
+                f.Bn[0][o] = bown[0];
+                f.Bn[1][o] = bown[1];
+                f.Bn[2][o] = bown[2];
+            }
+            sB[(0 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[0];
+            sB[(1 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[1];
+            sB[(2 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[2];
+            if (halo_col || halo_row) {
+                float hb[3] = {0.f, 0.f, 0.f};
+                if (halo_valid)
+                    compute_B<DIM, PML>(g, f, sc, sn, hlx, hly, hgi, hgj, k, halo_col ? 6 : 5, false,
+                                        hb);
+                for (int c = 0; c < 3; ++c) sB[(c * (BY + 1) + hly + 1) * (BX + 1) + hlx + 1] = hb[c];
+            }
+            __syncthreads();  // B: sB of plane k complete
+            if (!own) return;
             auto SB = [&](int c, int ly, int lx) {
                 return sB[(c * (BY + 1) + ly + 1) * (BX + 1) + lx + 1];
             };
@@ -382,25 +395,37 @@ __global__ void __launch_bounds__(NT, 4)
                     else jz += sv;
                 }
             }
-            const long long px = psi_index(g, f, 0, i, j, k);
-            const long long py = psi_index(g, f, 1, i, j, k);
-            const long long pz = DIM == 3 ? psi_index(g, f, 2, i, j, k) : -1;
             const float bx = SB(0, ty, tx), by = SB(1, ty, tx), bz = SB(2, ty, tx);
-            float tExy = cpml_term(f, 1, 0, py, j, false, (bz - SB(2, ty - 1, tx)) * g.inv_d[1], true);
+            float tExy = (bz - SB(2, ty - 1, tx)) * g.inv_d[1];
             float tExz = 0.f, tEyz = 0.f;
             if (DIM == 3) {
-                tExz = cpml_term(f, 2, 0, pz, k, false, (by - By_prev) * g.inv_d[2], true);
-                tEyz = cpml_term(f, 2, 1, pz, k, false, (bx - Bx_prev) * g.inv_d[2], true);
+                tExz = (by - By_prev) * g.inv_d[2];
+                tEyz = (bx - Bx_prev) * g.inv_d[2];
             }
-            float tEyx = cpml_term(f, 0, 0, px, i, false, (bz - SB(2, ty, tx - 1)) * g.inv_d[0], true);
-            float tEzx = cpml_term(f, 0, 1, px, i, false, (by - SB(1, ty, tx - 1)) * g.inv_d[0], true);
-            float tEzy = cpml_term(f, 1, 1, py, j, false, (bx - SB(0, ty - 1, tx)) * g.inv_d[1], true);
+            float tEyx = (bz - SB(2, ty, tx - 1)) * g.inv_d[0];
+            float tEzx = (by - SB(1, ty, tx - 1)) * g.inv_d[0];
+            float tEzy = (bx - SB(0, ty - 1, tx)) * g.inv_d[1];
+            if (PML) {
+                const long long px = psi_index(g, f, 0, i, j, k);
+                const long long py = psi_index(g, f, 1, i, j, k);
+                const long long pz = DIM == 3 ? psi_index(g, f, 2, i, j, k) : -1;
+                tExy = cpml_term(f, 1, 0, py, j, false, tExy, true);
+                if (DIM == 3) {
+                    tExz = cpml_term(f, 2, 0, pz, k, false, tExz, true);
+                    tEyz = cpml_term(f, 2, 1, pz, k, false, tEyz, true);
+                }
+                tEyx = cpml_term(f, 0, 0, px, i, false, tEyx, true);
+                tEzx = cpml_term(f, 0, 1, px, i, false, tEzx, true);
+                tEzy = cpml_term(f, 1, 1, py, j, false, tEzy, true);
+            }
             f.En[0][o] = te(sc, 0, tx, ty) + f.c2dt * (tExy - tExz) - f.dt_eps0 * jx;
             f.En[1][o] = te(sc, 1, tx, ty) + f.c2dt * (tEyz - tEyx) - f.dt_eps0 * jy;
             f.En[2][o] = te(sc, 2, tx, ty) + f.c2dt * (tEzx - tEzy) - f.dt_eps0 * jz;
             Bx_prev = bx;
             By_prev = by;
-        }
+        };
+        if (xyslab || zslab(k)) plane(std::true_type{});
+        else plane(std::false_type{});
     }
     __syncthreads();
     if (threadIdx.x == 0) {
