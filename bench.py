@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--grid", type=int, default=256, help="cells per side (256 = the workload)")
     ap.add_argument("--tile", type=str, default="", help="particle tile, e.g. 8,8,4")
     ap.add_argument("--sort-interval", type=int, default=0)
+    ap.add_argument("--tile-order", type=int, default=0)
     return ap.parse_args()
 
 
@@ -230,6 +231,8 @@ def run_gpu(args):
         tuning["tile"] = tuple(int(x) for x in args.tile.split(","))
     if args.sort_interval:
         tuning["sort_interval"] = args.sort_interval
+    if args.tile_order:
+        tuning["tile_order"] = args.tile_order
     h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning)
     diag0 = pic.pic_diagnostics(h)
     nparts = sum(diag0["count"])

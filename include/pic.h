@@ -145,6 +145,7 @@ typedef struct pic_tuning {
     int keep_J;         /* 1: J of the last step stays readable (tests) [0] */
     int timing;         /* 1: time every kernel launch with CUDA events [0] */
     int field_plain;    /* 1: field kernel with plain loads even where TMA applies [0] */
+    int tile_order;     /* particles inside a tile: 0 spread over cells, 1 cell order [0] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */

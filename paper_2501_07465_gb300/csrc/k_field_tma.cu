@@ -132,6 +132,74 @@ struct Stage {
     float *J[3];
 };
 
+// tile coordinates: E/B tiles start at (i0-4, j0-1): local (lx, ly) -> (lx+4, ly+1)
+__device__ inline float te(const Stage &s, int c, int lx, int ly) {
+    return s.E[c][(ly + 1) * EW + lx + 4];
+}
+__device__ inline float tb(const Stage &s, int c, int lx, int ly) {
+    return s.B[c][(ly + 1) * BW + lx + 4];
+}
+
+// CPML memory terms of one cell for one plane, loaded together at the start
+// of the plane so that their latencies overlap.  Slot order per axis (see
+// FieldP): x: E_y, E_z, B_y, B_z; y: E_x, E_z, B_x, B_z; z: E_x, E_y, B_x, B_y.
+struct PsiCell {
+    long long idx[3];   // slab index per axis or -1
+    float v[3][4];      // psi_in values
+};
+
+template <int DIM>
+__device__ inline void psi_load(const GridP &g, const FieldP &f, int i, int j, int k, PsiCell &pc) {
+    pc.idx[0] = psi_index(g, f, 0, i, j, k);
+    pc.idx[1] = psi_index(g, f, 1, i, j, k);
+    pc.idx[2] = DIM == 3 ? psi_index(g, f, 2, i, j, k) : -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            pc.v[a][q] = pc.idx[a] >= 0 ? __ldg(f.psi_in[a][q] + pc.idx[a]) : 0.f;
+}
+
+// derivative + updated memory term, with psi_in preloaded
+__device__ inline float cpml_pre(const FieldP &f, const PsiCell &pc, int a, int slot, int pos,
+                                 bool half, float deriv) {
+    if (pc.idx[a] < 0) return deriv;
+    float b = half ? __ldg(f.cb_h[a] + pos) : __ldg(f.cb_e[a] + pos);
+    float c = half ? __ldg(f.ca_h[a] + pos) : __ldg(f.ca_e[a] + pos);
+    float psi = b * pc.v[a][slot] + c * deriv;
+    f.psi_out[a][slot][pc.idx[a]] = psi;
+    return deriv + psi;
+}
+
+// B^{n+1/2} of an own cell in a CPML plane, memory terms preloaded
+template <int DIM>
+__device__ inline void compute_B_own_pml(const GridP &g, const FieldP &f, const Stage &cur,
+                                         const Stage &nxt, int lx, int ly, int gi, int gj, int k,
+                                         const PsiCell &pc, float *out) {
+    const float dt = g.dt;
+    float dEz_dy = (te(cur, 2, lx, ly + 1) - te(cur, 2, lx, ly)) * g.inv_d[1];
+    float t1 = cpml_pre(f, pc, 1, 2, gj, true, dEz_dy);
+    float t2 = 0.f;
+    if (DIM == 3) {
+        float dEy_dz = (te(nxt, 1, lx, ly) - te(cur, 1, lx, ly)) * g.inv_d[2];
+        t2 = cpml_pre(f, pc, 2, 2, k, true, dEy_dz);
+    }
+    out[0] = tb(cur, 0, lx, ly) - dt * (t1 - t2);
+    t1 = 0.f;
+    if (DIM == 3) {
+        float dEx_dz = (te(nxt, 0, lx, ly) - te(cur, 0, lx, ly)) * g.inv_d[2];
+        t1 = cpml_pre(f, pc, 2, 3, k, true, dEx_dz);
+    }
+    float dEz_dx = (te(cur, 2, lx + 1, ly) - te(cur, 2, lx, ly)) * g.inv_d[0];
+    t2 = cpml_pre(f, pc, 0, 2, gi, true, dEz_dx);
+    out[1] = tb(cur, 1, lx, ly) - dt * (t1 - t2);
+    float dEy_dx = (te(cur, 1, lx + 1, ly) - te(cur, 1, lx, ly)) * g.inv_d[0];
+    float dEx_dy = (te(cur, 0, lx, ly + 1) - te(cur, 0, lx, ly)) * g.inv_d[1];
+    t1 = cpml_pre(f, pc, 0, 3, gi, true, dEy_dx);
+    t2 = cpml_pre(f, pc, 1, 3, gj, true, dEx_dy);
+    out[2] = tb(cur, 2, lx, ly) - dt * (t1 - t2);
+}
+
 __device__ inline Stage stage_ptrs(unsigned char *smem, int slot) {
     Stage st;
     unsigned char *base = smem + (size_t)slot * STAGE;
@@ -141,14 +209,6 @@ __device__ inline Stage stage_ptrs(unsigned char *smem, int slot) {
         st.J[c] = reinterpret_cast<float *>(base + 3 * E_PAD + 3 * B_PAD + c * J_PAD);
     }
     return st;
-}
-
-// tile coordinates: E/B tiles start at (i0-4, j0-1): local (lx, ly) -> (lx+4, ly+1)
-__device__ inline float te(const Stage &s, int c, int lx, int ly) {
-    return s.E[c][(ly + 1) * EW + lx + 4];
-}
-__device__ inline float tb(const Stage &s, int c, int lx, int ly) {
-    return s.B[c][(ly + 1) * BW + lx + 4];
 }
 
 // B^{n+1/2} at local (lx, ly) of plane k (global gi, gj, k in the domain).
@@ -354,8 +414,11 @@ __global__ void __launch_bounds__(NT, 4)
         auto plane = [&](auto pml_tag) {
             constexpr bool PML = decltype(pml_tag)::value;
             float bown[3] = {0.f, 0.f, 0.f};
+            PsiCell pc;
+            if (PML && own) psi_load<DIM>(g, f, i, j, k, pc);
             if (own) {
-                compute_B<DIM, PML>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
+                if (PML) compute_B_own_pml<DIM>(g, f, sc, sn, tx, ty, i, j, k, pc, bown);
+                else compute_B<DIM, false>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
                 f.Bn[0][o] = bown[0];
                 f.Bn[1][o] = bown[1];
                 f.Bn[2][o] = bown[2];
@@ -406,17 +469,14 @@ __global__ void __launch_bounds__(NT, 4)
             float tEzx = (by - SB(1, ty, tx - 1)) * g.inv_d[0];
             float tEzy = (bx - SB(0, ty - 1, tx)) * g.inv_d[1];
             if (PML) {
-                const long long px = psi_index(g, f, 0, i, j, k);
-                const long long py = psi_index(g, f, 1, i, j, k);
-                const long long pz = DIM == 3 ? psi_index(g, f, 2, i, j, k) : -1;
-                tExy = cpml_term(f, 1, 0, py, j, false, tExy, true);
+                tExy = cpml_pre(f, pc, 1, 0, j, false, tExy);
                 if (DIM == 3) {
-                    tExz = cpml_term(f, 2, 0, pz, k, false, tExz, true);
-                    tEyz = cpml_term(f, 2, 1, pz, k, false, tEyz, true);
+                    tExz = cpml_pre(f, pc, 2, 0, k, false, tExz);
+                    tEyz = cpml_pre(f, pc, 2, 1, k, false, tEyz);
                 }
-                tEyx = cpml_term(f, 0, 0, px, i, false, tEyx, true);
-                tEzx = cpml_term(f, 0, 1, px, i, false, tEzx, true);
-                tEzy = cpml_term(f, 1, 1, py, j, false, tEzy, true);
+                tEyx = cpml_pre(f, pc, 0, 0, i, false, tEyx);
+                tEzx = cpml_pre(f, pc, 0, 1, i, false, tEzx);
+                tEzy = cpml_pre(f, pc, 1, 1, j, false, tEzy);
             }
             f.En[0][o] = te(sc, 0, tx, ty) + f.c2dt * (tExy - tExz) - f.dt_eps0 * jx;
             f.En[1][o] = te(sc, 1, tx, ty) + f.c2dt * (tEyz - tEyx) - f.dt_eps0 * jy;

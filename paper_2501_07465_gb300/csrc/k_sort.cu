@@ -104,7 +104,8 @@ __device__ inline void mv(T *dst, const T *src, long long d, long long s) {
 }
 
 __global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_src, SpeciesP dst,
-                                    uint32_t *pid_dst, const int *start, const int *rank) {
+                                    uint32_t *pid_dst, const int *start, const int *rank,
+                                    int spread) {
     const long long n = src.n;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
@@ -117,7 +118,7 @@ __global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_
         long long P = 7919;
         if (cnt % P == 0) P = 7907;
         if (cnt % P == 0) P = 7901;
-        long long d = (long long)start[t] + ((long long)rank[p] * P) % cnt;
+        long long d = (long long)start[t] + (spread ? ((long long)rank[p] * P) % cnt : rank[p]);
         dst.cell[d] = c;
         pid_dst[d] = pid_src[p];
         for (int a = 0; a < 3; ++a) mv(dst.v[a], src.v[a], d, p);
@@ -222,11 +223,11 @@ cudaError_t launch_scan_int(const int *in, int *out_excl, long long n, int *tmp,
 
 cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
                                 const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
-                                const int *start, const int *rank, cudaStream_t s) {
+                                const int *start, const int *rank, bool spread, cudaStream_t s) {
     (void)g;
     if (src.n <= 0) return cudaSuccess;
     tile_scatter_kernel<<<grid_for(src.n, 256), 256, 0, s>>>(tp, src, pid_src, dst, pid_dst, start,
-                                                             rank);
+                                                             rank, spread ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -257,7 +257,7 @@ pic_status sort_species(pic_sim *s, int i) {
     CK(s, launch_tile_histogram(s->g, tp, src.cell, sp.n, s->sort_count, s->sort_rank, s->stream));
     CK(s, launch_scan_int(s->sort_count, sp.tile_start, tp.ntiles, s->scan_tmp, 0, s->stream));
     CK(s, launch_tile_scatter(s->g, tp, src, sp.pid[sp.cur], dst, sp.pid[1 - sp.cur],
-                              sp.tile_start, s->sort_rank, s->stream));
+                              sp.tile_start, s->sort_rank, s->tun.tile_order == 0, s->stream));
     s->launches += 2 + scan_kernel_count(tp.ntiles);
     sp.cur = 1 - sp.cur;
     return PIC_OK;
@@ -558,6 +558,7 @@ pic_status pic_set_tuning(pic_sim *s, const pic_tuning *t) {
     nt.keep_J = t->keep_J;
     nt.timing = t->timing;
     nt.field_plain = t->field_plain;
+    nt.tile_order = t->tile_order;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;

@@ -150,7 +150,7 @@ long long scan_tmp_len(long long n);
 int scan_kernel_count(long long n);
 cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
                                 const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
-                                const int *start, const int *rank, cudaStream_t s);
+                                const int *start, const int *rank, bool spread, cudaStream_t s);
 cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,
                                      int *active, int *nactive, int *work, cudaStream_t s);
 cudaError_t launch_cell_histogram(const GridP &g, const SpeciesP &sp, int *counts,
