@@ -232,6 +232,48 @@ pic_status pic_memory_bytes(const pic_sim *sim, size_t *bytes);
 /* Text of the last error on this handle (never NULL). */
 const char *pic_last_error(const pic_sim *sim);
 
+/* ------------------------------------------------------------------------
+   Batch engine: many independent simulations (for example nanostructures of
+   uneven size) advanced by the same launches.
+   A group holds up to `capacity` simulations of one dimensionality and one
+   particle tile size (the first member fixes both).  pic_group_step advances
+   every member that has steps left -- a member added with nsteps stops after
+   nsteps -- with one persistent launch for the particle phase of all members
+   and one launch for their field phase per step; the tile re-sorts of all
+   members run in a few batched launches every sort_interval steps (the first
+   member's interval).  With use_graph the steps between re-sorts are captured
+   once into a CUDA graph and replayed; finished members are skipped on the
+   device.  While in a group a member cannot be stepped on its own, nor take
+   a mask, species or tuning (PIC_ESTATE); pic_read_*, pic_write_fields,
+   pic_diagnostics and pic_sync on a member wait for the group's stream, and
+   pic_destroy on a member removes it first.  Admission: the device bytes of
+   all members must stay within hbm_budget (0 = no limit; PIC_EBUDGET
+   otherwise, also when all `capacity` slots are taken).
+   stream: the CUDA stream all group work is queued on; NULL makes the group
+   create (and later destroy) a non-blocking stream of its own, since the
+   legacy default stream cannot be captured into a graph.  The group keeps
+   small device tables (parameter blocks, work-item lists, sort scratch of one
+   int per mobile particle) that it allocates through the pic_set_allocator
+   hooks when membership changes.
+   ------------------------------------------------------------------------ */
+pic_status pic_group_create(int capacity, size_t hbm_budget, void *stream, int use_graph,
+                            pic_group **out);
+/* Free the group; members are released (their handles stay valid). */
+pic_status pic_group_destroy(pic_group *g);
+/* Add a simulation that will advance nsteps more steps with the group. */
+pic_status pic_group_add(pic_group *g, pic_sim *sim, int64_t nsteps);
+/* Remove a member (after waiting for the group's stream). */
+pic_status pic_group_remove(pic_group *g, pic_sim *sim);
+/* Enqueue nsteps group steps (asynchronous). */
+pic_status pic_group_step(pic_group *g, int nsteps);
+/* Wait for the group's stream; return a latched device error of any member. */
+pic_status pic_group_sync(pic_group *g);
+/* Steps a member has taken in the group and steps it has left. */
+pic_status pic_group_progress(pic_group *g, const pic_sim *sim, int64_t *steps_done,
+                              int64_t *steps_left);
+/* Members, device bytes held by members, kernels launched since creation. */
+pic_status pic_group_info(pic_group *g, int *members, size_t *member_bytes, int64_t *launches);
+
 /* Largest grid (cells) pic_cell_counts_noalloc accepts: 2^22 cells, i.e. a
    16 MiB int32 array built into the library. */
 #define PIC_NOALLOC_MAX_CELLS (1 << 22)

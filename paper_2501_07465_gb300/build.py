@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
-SOURCES = ["pic_api.cu", "k_field.cu", "k_field_tma.cu", "k_particle.cu", "k_sort.cu", "k_fd.cu",
-           "k_diag.cu"]
+SOURCES = ["pic_api.cu", "pic_group.cu", "k_field.cu", "k_field_tma.cu", "k_particle.cu",
+           "k_sort.cu", "k_fd.cu", "k_diag.cu", "k_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -37,7 +37,8 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "pic_internal.cuh"), os.path.join(INCLUDE, "pic.h")]
+    headers = [os.path.join(CSRC, "pic_internal.cuh"), os.path.join(CSRC, "pic_sim.h"),
+               os.path.join(INCLUDE, "pic.h")]
     cc = nvcc()
     extra = list(extra or [])
 

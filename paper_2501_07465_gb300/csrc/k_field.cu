@@ -134,22 +134,26 @@ __device__ inline void compute_B(const GridP &g, const FieldP &f, float (*cur)[S
     }
 }
 
+// One 32 x 8 column block (block coordinates bx, by, chunk bz) of one
+// simulation.  g and f must live in parameter or shared memory.
 template <int DIM>
-__global__ void __launch_bounds__(BX * BY) field_kernel(GridP g, FieldP f) {
+__device__ void field_block(const GridP &g, const FieldP &f, const int blk_x, const int blk_y,
+                            const int blk_z) {
     __shared__ float sE[2][3][SY][SX];
     __shared__ float sB[3][BY + 1][BX + 1];  // local [-1, BY) x [-1, BX)
     __shared__ double s_src;
 
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i0 = blk_x * BX, j0 = blk_y * BY;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int i = i0 + tx, j = j0 + ty;
     const bool own = (i < nx) && (j < ny);
-    const int kbeg = DIM == 3 ? blockIdx.z * f.zchunk : 0;
+    const int kbeg = DIM == 3 ? blk_z * f.zchunk : 0;
     const int kend = DIM == 3 ? min(kbeg + f.zchunk, nz) : 1;
 
-    const long long bflag = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
+    const long long bflag = ((long long)blk_z * f.nby + blk_y) * f.nbx + blk_x;
     const bool jdirty = f.jdirty[bflag] != 0;
+    __syncthreads();  // every thread has read the flag (cleared at the end)
 
     if (threadIdx.x == 0) {
         double v = 0.0;
@@ -273,7 +277,43 @@ __global__ void __launch_bounds__(BX * BY) field_kernel(GridP g, FieldP f) {
     if (threadIdx.x == 0 && jdirty) f.jdirty_clear[bflag] = 0;
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(BX * BY) field_kernel(GridP g, FieldP f) {
+    field_block<DIM>(g, f, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Many simulations in one launch: one CTA per item (simulation, bx, by, bz);
+// the simulation's parameter blocks (FieldP per field ping-pong parity) are
+// copied to shared memory.
+template <int DIM>
+__global__ void __launch_bounds__(BX * BY)
+    batch_field_kernel(const GridP *grids, const FieldP *fdescs, const int *fpar, const int *active,
+                       const int4 *items) {
+    __shared__ GridP sg;
+    __shared__ FieldP sf;
+    const int4 w = items[blockIdx.x];
+    if (!active[w.x]) return;
+    {
+        const int *src = reinterpret_cast<const int *>(grids + w.x);
+        int *dst = reinterpret_cast<int *>(&sg);
+        for (int q = threadIdx.x; q < (int)(sizeof(GridP) / 4); q += blockDim.x) dst[q] = src[q];
+        src = reinterpret_cast<const int *>(fdescs + 2 * w.x + fpar[w.x]);
+        dst = reinterpret_cast<int *>(&sf);
+        for (int q = threadIdx.x; q < (int)(sizeof(FieldP) / 4); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    field_block<DIM>(sg, sf, w.y, w.z, w.w);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
+                               const int *active, const int4 *items, int nitems, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (dims == 3) batch_field_kernel<3><<<nitems, BX * BY, 0, s>>>(grids, fdescs, fpar, active, items);
+    else batch_field_kernel<2><<<nitems, BX * BY, 0, s>>>(grids, fdescs, fpar, active, items);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s) {
     dim3 block(BX * BY);

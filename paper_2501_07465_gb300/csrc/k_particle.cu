@@ -632,10 +632,12 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, lo
 // the kernel
 // ---------------------------------------------------------------------------
 
+// One tile of one simulation: stage the field box, push every particle of
+// the tile (all species), flush the J box.  P must live in parameter or shared
+// memory (not global), so that the compiler keeps its fields in registers
+// across the particle stores.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
-    extern __shared__ float smem[];
-    __shared__ unsigned s_refl[kMaxSpecies];
+__device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, unsigned *s_refl) {
     const TileP &tp = P.tp;
     const int bn = tp.boxn;
     BoxAcc box;
@@ -653,120 +655,154 @@ __global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
     glob.nbx = P.nbx;
     glob.nby = P.nby;
     glob.zchunk = P.zchunk;
-
-    if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *P.step_counter += 1;
-
     const GridP &g = P.g;
-    const int nact = *P.nactive;
     const float hdt = 0.5f * g.dt;
-    for (int it = blockIdx.x; it < nact; it += gridDim.x) {
-        const int t = P.active[it];
-        const int tx = t % tp.nt[0], ty = (t / tp.nt[0]) % tp.nt[1], tz = t / (tp.nt[0] * tp.nt[1]);
-        const int org[3] = {tx * tp.T[0], ty * tp.T[1], DIM == 3 ? tz * tp.T[2] : 0};
-        __syncthreads();  // previous tile's flush is done with the box
-        // stage E^n, B^{n-1/2} of the box; zero J
-        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-            bool in = gx >= 0 && gy >= 0 && gz >= 0;
-            long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
-            for (int c = 0; c < 3; ++c) {
-                box.F[c][e] = in ? __ldg(P.E[c] + o) : 0.f;
-                box.F[3 + c][e] = in ? __ldg(P.B[c] + o) : 0.f;
-                box.J[c][e] = 0.f;
-            }
-        }
-        __syncthreads();
-        // B^n = B^{n-1/2} - (dt/2) curl E^n (plain Yee curl); zero outside
-        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-            bool hx = bx + 1 < tp.box[0], hy = by + 1 < tp.box[1];
-            bool hz = DIM == 2 || bz + 1 < tp.box[2];
-            if (!(hx && hy && hz)) continue;  // never gathered
-            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-            if (gx < 0 || gy < 0 || gz < 0) {
-                box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
-                continue;
-            }
-            const int sx = 1, sy = box.b0, sz = box.b01;
-            float dEz_dy = (box.F[2][e + sy] - box.F[2][e]) * g.inv_d[1];
-            float dEx_dy = (box.F[0][e + sy] - box.F[0][e]) * g.inv_d[1];
-            float dEz_dx = (box.F[2][e + sx] - box.F[2][e]) * g.inv_d[0];
-            float dEy_dx = (box.F[1][e + sx] - box.F[1][e]) * g.inv_d[0];
-            float dEy_dz = 0.f, dEx_dz = 0.f;
-            if (DIM == 3) {
-                dEy_dz = (box.F[1][e + sz] - box.F[1][e]) * g.inv_d[2];
-                dEx_dz = (box.F[0][e + sz] - box.F[0][e]) * g.inv_d[2];
-            }
-            box.F[3][e] -= hdt * (dEz_dy - dEy_dz);
-            box.F[4][e] -= hdt * (dEx_dz - dEz_dx);
-            box.F[5][e] -= hdt * (dEy_dx - dEx_dy);
-        }
-        __syncthreads();
-        for (int si = 0; si < P.nsp; ++si) {
-            const SpeciesP &s = P.sp[si];
-            const long long a = s.tile_start[t], b = s.tile_start[t + 1];
-            unsigned r = 0;
-            if (s.kind == PIC_BOUND) {
-                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                    push_bound<DIM>(P, s, p, org, box, glob);
-            } else if (s.kind == PIC_DIRAC) {
-                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                    r += push_mobile<DIM, PIC_DIRAC>(P, s, p, org, box, glob);
-            } else {
-                for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                    r += push_mobile<DIM, PIC_FREE>(P, s, p, org, box, glob);
-            }
-            if (r) atomicAdd(&s_refl[si], r);
-        }
-        __syncthreads();
-        // flush the J tile
-        for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-            int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-            float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
-            if (jx == 0.f && jy == 0.f && jz == 0.f) continue;
-            int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-            if (gx < 0 || gy < 0 || gz < 0) continue;
-            long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
-            if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
-            if (jy != 0.f) atomicAdd(P.J[1] + o, jy);
-            if (jz != 0.f) atomicAdd(P.J[2] + o, jz);
-        }
-        // mark the field blocks the box overlaps
-        if (threadIdx.x == 0) {
-            int bl[3][kMaxBlocksPerAxis], nb[3];
-            const int fb[3] = {kFieldBX, kFieldBY, P.zchunk};
-            for (int ax = 0; ax < 3; ++ax) {
-                nb[ax] = 0;
-                if (ax == 2 && DIM == 2) { bl[2][0] = 0; nb[2] = 1; continue; }
-                for (int c = org[ax] - kHalo; c < org[ax] + tp.T[ax] + kHalo + 1; ++c) {
-                    int gc = wrap_or_neg(c, g.n[ax], g.per[ax]);
-                    if (gc < 0) continue;
-                    int blk = gc / fb[ax];
-                    bool seen = false;
-                    for (int q = 0; q < nb[ax]; ++q) seen = seen || bl[ax][q] == blk;
-                    if (!seen) {
-                        if (nb[ax] < kMaxBlocksPerAxis) bl[ax][nb[ax]++] = blk;
-                        else atomicOr(P.status, kStatusBounds);
-                    }
-                }
-            }
-            for (int z = 0; z < nb[2]; ++z)
-                for (int y = 0; y < nb[1]; ++y)
-                    for (int x = 0; x < nb[0]; ++x)
-                        P.jdirty[((long long)bl[2][z] * P.nby + bl[1][y]) * P.nbx + bl[0][x]] = 1;
+    const int tx = t % tp.nt[0], ty = (t / tp.nt[0]) % tp.nt[1], tz = t / (tp.nt[0] * tp.nt[1]);
+    const int org[3] = {tx * tp.T[0], ty * tp.T[1], DIM == 3 ? tz * tp.T[2] : 0};
+    __syncthreads();  // previous tile's flush is done with the box
+    // stage E^n, B^{n-1/2} of the box; zero J
+    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+        bool in = gx >= 0 && gy >= 0 && gz >= 0;
+        long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
+        for (int c = 0; c < 3; ++c) {
+            box.F[c][e] = in ? __ldg(P.E[c] + o) : 0.f;
+            box.F[3 + c][e] = in ? __ldg(P.B[c] + o) : 0.f;
+            box.J[c][e] = 0.f;
         }
     }
     __syncthreads();
+    // B^n = B^{n-1/2} - (dt/2) curl E^n (plain Yee curl); zero outside
+    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+        bool hx = bx + 1 < tp.box[0], hy = by + 1 < tp.box[1];
+        bool hz = DIM == 2 || bz + 1 < tp.box[2];
+        if (!(hx && hy && hz)) continue;  // never gathered
+        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+        if (gx < 0 || gy < 0 || gz < 0) {
+            box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
+            continue;
+        }
+        const int sx = 1, sy = box.b0, sz = box.b01;
+        float dEz_dy = (box.F[2][e + sy] - box.F[2][e]) * g.inv_d[1];
+        float dEx_dy = (box.F[0][e + sy] - box.F[0][e]) * g.inv_d[1];
+        float dEz_dx = (box.F[2][e + sx] - box.F[2][e]) * g.inv_d[0];
+        float dEy_dx = (box.F[1][e + sx] - box.F[1][e]) * g.inv_d[0];
+        float dEy_dz = 0.f, dEx_dz = 0.f;
+        if (DIM == 3) {
+            dEy_dz = (box.F[1][e + sz] - box.F[1][e]) * g.inv_d[2];
+            dEx_dz = (box.F[0][e + sz] - box.F[0][e]) * g.inv_d[2];
+        }
+        box.F[3][e] -= hdt * (dEz_dy - dEy_dz);
+        box.F[4][e] -= hdt * (dEx_dz - dEz_dx);
+        box.F[5][e] -= hdt * (dEy_dx - dEx_dy);
+    }
+    __syncthreads();
+    for (int si = 0; si < P.nsp; ++si) {
+        const SpeciesP &s = P.sp[si];
+        const long long a = s.tile_start[t], b = s.tile_start[t + 1];
+        unsigned r = 0;
+        if (s.kind == PIC_BOUND) {
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                push_bound<DIM>(P, s, p, org, box, glob);
+        } else if (s.kind == PIC_DIRAC) {
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                r += push_mobile<DIM, PIC_DIRAC>(P, s, p, org, box, glob);
+        } else {
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
+                r += push_mobile<DIM, PIC_FREE>(P, s, p, org, box, glob);
+        }
+        if (r) atomicAdd(&s_refl[si], r);
+    }
+    __syncthreads();
+    // flush the J tile
+    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
+        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
+        float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
+        if (jx == 0.f && jy == 0.f && jz == 0.f) continue;
+        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
+        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
+        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
+        if (gx < 0 || gy < 0 || gz < 0) continue;
+        long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+        if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
+        if (jy != 0.f) atomicAdd(P.J[1] + o, jy);
+        if (jz != 0.f) atomicAdd(P.J[2] + o, jz);
+    }
+    // mark the field blocks the box overlaps
+    if (threadIdx.x == 0) {
+        int bl[3][kMaxBlocksPerAxis], nb[3];
+        const int fb[3] = {kFieldBX, kFieldBY, P.zchunk};
+        for (int ax = 0; ax < 3; ++ax) {
+            nb[ax] = 0;
+            if (ax == 2 && DIM == 2) { bl[2][0] = 0; nb[2] = 1; continue; }
+            for (int c = org[ax] - kHalo; c < org[ax] + tp.T[ax] + kHalo + 1; ++c) {
+                int gc = wrap_or_neg(c, g.n[ax], g.per[ax]);
+                if (gc < 0) continue;
+                int blk = gc / fb[ax];
+                bool seen = false;
+                for (int q = 0; q < nb[ax]; ++q) seen = seen || bl[ax][q] == blk;
+                if (!seen) {
+                    if (nb[ax] < kMaxBlocksPerAxis) bl[ax][nb[ax]++] = blk;
+                    else atomicOr(P.status, kStatusBounds);
+                }
+            }
+        }
+        for (int z = 0; z < nb[2]; ++z)
+            for (int y = 0; y < nb[1]; ++y)
+                for (int x = 0; x < nb[0]; ++x)
+                    P.jdirty[((long long)bl[2][z] * P.nby + bl[1][y]) * P.nbx + bl[0][x]] = 1;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
+    extern __shared__ float smem[];
+    __shared__ unsigned s_refl[kMaxSpecies];
+    if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.step_counter) *P.step_counter += 1;
+    const int nact = *P.nactive;
+    for (int it = blockIdx.x; it < nact; it += gridDim.x) tile_pass<DIM>(P, P.active[it], smem, s_refl);
+    __syncthreads();
     if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
         atomicAdd(P.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
+}
+
+// Many simulations in one persistent launch: items[i] = (simulation, tile),
+// tile < 0 = padding.  Each simulation's parameter block (two variants, one
+// per field ping-pong parity) is copied to shared memory for its items.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+    batch_particle_kernel(const ParticleLaunch *descs, const int *fpar, const int *active,
+                          const int2 *items, int nitems) {
+    extern __shared__ float smem[];
+    __shared__ unsigned s_refl[kMaxSpecies];
+    __shared__ ParticleLaunch sP;
+    __shared__ int s_sim;
+    if (threadIdx.x == 0) s_sim = -1;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        if (w.y < 0 || !active[w.x]) continue;  // uniform over the CTA
+        __syncthreads();  // previous item finished with sP / s_refl
+        if (s_sim != w.x) {
+            const int *src = reinterpret_cast<const int *>(descs + 2 * w.x + fpar[w.x]);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int q = threadIdx.x; q < (int)(sizeof(ParticleLaunch) / 4); q += blockDim.x)
+                dst[q] = src[q];
+        }
+        if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) s_sim = w.x;
+        tile_pass<DIM>(sP, w.y, smem, s_refl);
+        __syncthreads();
+        if (threadIdx.x < sP.nsp && s_refl[threadIdx.x])
+            atomicAdd(sP.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
+    }
 }
 
 }  // namespace
@@ -775,6 +811,10 @@ size_t particle_smem_bytes(const TileP &tp) { return (size_t)9 * tp.boxn * sizeo
 
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm) {
     cudaError_t e;
+    e = cudaFuncSetAttribute(dims == 3 ? (const void *)batch_particle_kernel<3>
+                                       : (const void *)batch_particle_kernel<2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     if (dims == 3) {
         e = cudaFuncSetAttribute(particle_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -787,6 +827,16 @@ cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm) {
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<2>, kThreads,
                                                          smem);
+}
+
+cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
+                                  const int *active, const int2 *items, int nitems, int nctas,
+                                  size_t smem, cudaStream_t s) {
+    if (nctas < 1) nctas = 1;
+    if (dims == 3)
+        batch_particle_kernel<3><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems);
+    else batch_particle_kernel<2><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s) {

@@ -9,9 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "pic_internal.cuh"
-
-using namespace pic;
+#include "pic_sim.h"
 
 namespace {
 
@@ -23,78 +21,9 @@ struct Allocator {
 Allocator g_alloc;
 thread_local std::string g_err;
 
-struct DevBuf {
-    void *p;
-    size_t bytes;
-};
-
-struct Species {
-    pic_species_desc desc{};
-    long long n = 0;
-    double weight = 0;
-    int cur = 0;
-    uint32_t *cell[2] = {nullptr, nullptr};
-    uint32_t *pid[2] = {nullptr, nullptr};
-    float *o[2][3] = {};
-    float *v[2][3] = {};
-    double *anchor[2][3] = {};
-    float *anchor32[2][3] = {};
-    float *disp[2][3] = {};
-    int *tile_start = nullptr;
-    unsigned long long *nrefl = nullptr;
-};
-
-struct TimedEvents {
-    std::vector<cudaEvent_t> start, stop;
-};
-
 }  // namespace
 
-struct pic_sim {
-    int device = 0;
-    int num_sms = 148;
-    cudaStream_t stream = nullptr;
-    pic_grid_desc gd{};
-    GridP g{};
-    TileP tp{};
-    pic_tuning tun{};
-    std::vector<DevBuf> bufs;
-    size_t bytes = 0;
-    float *E[2][3] = {};
-    float *B[2][3] = {};
-    float *J[3] = {};
-    int fcur = 0;
-    float *psi[2][3][4] = {};
-    float *cb_e[3] = {}, *ca_e[3] = {}, *cb_h[3] = {}, *ca_h[3] = {};
-    uint8_t *mask_d = nullptr;
-    std::vector<uint8_t> mask_h;
-    uint8_t *jdirty = nullptr;
-    int nbx = 1, nby = 1, nbz = 1;
-    double *rho_bg = nullptr, *rho = nullptr;
-    long long *step_counter = nullptr;
-    int *status = nullptr;
-    DiagAcc *diag_acc = nullptr;
-    // sort / tiles
-    int *active = nullptr, *nactive = nullptr;
-    int *tile_work = nullptr;
-    int *sort_count = nullptr, *sort_rank = nullptr, *scan_tmp = nullptr;
-    long long rank_cap = 0;
-    int **starts_dev = nullptr;
-    int particle_ctas = 1;
-    size_t psmem = 0;
-    int nsp = 0;
-    Species sp[kMaxSpecies];
-    long long steps = 0;
-    int since_sort = 0;
-    double omega_p2 = 0.0, omega_b2 = 0.0;
-    std::string err;
-    TimedEvents ev[3];  // particle, field, sort
-    long long launches = 0;  // kernels launched by pic_step since the last timing query
-    TmaMaps maps;            // TMA descriptors of the field arrays
-    bool use_tma = false;    // TMA field kernel (needs nx % 4 == 0)
-};
-
-namespace {
+namespace pic {
 
 pic_status fail(pic_sim *s, pic_status st, const std::string &msg) {
     if (s) s->err = msg;
@@ -102,12 +31,7 @@ pic_status fail(pic_sim *s, pic_status st, const std::string &msg) {
     return st;
 }
 
-#define CK(sim, call)                                                                     \
-    do {                                                                                  \
-        cudaError_t _e = (call);                                                          \
-        if (_e != cudaSuccess)                                                            \
-            return fail(sim, PIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
-    } while (0)
+
 
 void *dalloc(pic_sim *s, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -126,6 +50,25 @@ void *dalloc(pic_sim *s, size_t bytes) {
     return p;
 }
 
+void *raw_alloc(size_t bytes, cudaStream_t stream) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (g_alloc.alloc) return g_alloc.alloc(bytes, (void *)stream, g_alloc.ctx);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void raw_free(void *p, size_t bytes, cudaStream_t stream) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (g_alloc.release) g_alloc.release(p, bytes, (void *)stream, g_alloc.ctx);
+    else cudaFree(p);
+}
+
 void dfree(pic_sim *s, void *p) {
     if (!p) return;
     for (size_t i = 0; i < s->bufs.size(); ++i) {
@@ -138,12 +81,6 @@ void dfree(pic_sim *s, void *p) {
     }
 }
 
-template <class T>
-bool alloc_zero(pic_sim *s, T **out, size_t count) {
-    *out = (T *)dalloc(s, count * sizeof(T));
-    if (!*out) return false;
-    return cudaMemsetAsync(*out, 0, count * sizeof(T), s->stream) == cudaSuccess;
-}
 
 double dt_limit(const pic_sim *s, double wb2, double wp2) {
     double inv = 1.0 / (s->gd.dx * s->gd.dx) + 1.0 / (s->gd.dy * s->gd.dy);
@@ -367,13 +304,14 @@ ParticleLaunch particle_params(pic_sim *s) {
 
 pic_status check_device_status(pic_sim *s) {
     int st = 0;
+    if (s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     CK(s, cudaMemcpy(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st & kStatusTimeout) return fail(s, PIC_ETIMEOUT, "device wait timed out");
     if (st & kStatusBounds) return fail(s, PIC_EBOUNDS, "device bounds check fired");
     return PIC_OK;
 }
 
-}  // namespace
+}  // namespace pic
 
 // ---------------------------------------------------------------------------
 // ABI
@@ -524,6 +462,7 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
 
 pic_status pic_destroy(pic_sim *s) {
     if (!s) return PIC_OK;
+    if (s->group) pic_group_remove(s->group, s);
     cudaStreamSynchronize(s->stream);
     for (auto &b : s->bufs) {
         if (g_alloc.release) g_alloc.release(b.p, b.bytes, (void *)s->stream, g_alloc.ctx);
@@ -539,6 +478,7 @@ pic_status pic_destroy(pic_sim *s) {
 
 pic_status pic_set_material_mask(pic_sim *s, const uint8_t *mask, size_t n) {
     if (!s || !mask) return fail(s, PIC_EINVAL, "null argument");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
     if ((long long)n != s->g.ncell) return fail(s, PIC_EINVAL, "mask size must equal the cell count");
     if (s->nsp > 0) return fail(s, PIC_ESTATE, "set the mask before loading species");
     if (!s->mask_d && !(s->mask_d = (uint8_t *)dalloc(s, n))) return fail(s, PIC_ENOMEM, "mask");
@@ -550,6 +490,15 @@ pic_status pic_set_material_mask(pic_sim *s, const uint8_t *mask, size_t n) {
 pic_status pic_set_tuning(pic_sim *s, const pic_tuning *t) {
     if (!s || !t) return fail(s, PIC_EINVAL, "null argument");
     if (s->steps > 0) return fail(s, PIC_ESTATE, "tuning must precede the first step");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    return pic::apply_tuning(s, t);
+}
+
+}  // extern "C"
+
+namespace pic {
+
+pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     pic_tuning nt = s->tun;
     for (int a = 0; a < 3; ++a)
         if (t->tile[a] > 0) nt.tile[a] = t->tile[a];
@@ -579,9 +528,14 @@ pic_status pic_set_tuning(pic_sim *s, const pic_tuning *t) {
     return PIC_OK;
 }
 
+}  // namespace pic
+
+extern "C" {
+
 pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_particles *pp,
                             int *species_id) {
     if (!s || !d || !pp) return fail(s, PIC_EINVAL, "null argument");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
     if (s->nsp >= kMaxSpecies) return fail(s, PIC_EINVAL, "too many species");
     if (d->kind != PIC_FREE && d->kind != PIC_BOUND && d->kind != PIC_DIRAC)
         return fail(s, PIC_EINVAL, "unknown species kind");
@@ -766,6 +720,7 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
 
 pic_status pic_step(pic_sim *s, int nsteps) {
     if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation steps through its group");
     if (nsteps < 0) return fail(s, PIC_EINVAL, "nsteps must be >= 0");
     const long long nc = s->g.ncell;
     for (int it = 0; it < nsteps; ++it) {
@@ -806,6 +761,7 @@ pic_status pic_sync(pic_sim *s) {
 }
 
 pic_status pic_read_fields(pic_sim *s, int which, double *out, size_t n) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     const long long nc = s->g.ncell;
     int cnt = 0;
@@ -828,6 +784,7 @@ pic_status pic_read_fields(pic_sim *s, int which, double *out, size_t n) {
 }
 
 pic_status pic_write_fields(pic_sim *s, int which, const double *in, size_t n) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !in) return fail(s, PIC_EINVAL, "null argument");
     const long long nc = s->g.ncell;
     int cnt = 0;
@@ -849,6 +806,7 @@ pic_status pic_write_fields(pic_sim *s, int which, const double *in, size_t n) {
 
 pic_status pic_read_species(pic_sim *s, int k, int32_t *cell, float *off, float *v,
                             double *anchor_off, float *disp, size_t n) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s) return fail(s, PIC_EINVAL, "null handle");
     if (k < 0 || k >= s->nsp) return fail(s, PIC_EINVAL, "no such species");
     Species &sp = s->sp[k];
@@ -879,6 +837,7 @@ pic_status pic_read_species(pic_sim *s, int k, int32_t *cell, float *off, float 
 }
 
 pic_status pic_cell_counts(pic_sim *s, int k, int32_t *out, size_t n) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     if (k < 0 || k >= s->nsp) return fail(s, PIC_EINVAL, "no such species");
     if ((long long)n != s->g.ncell) return fail(s, PIC_EINVAL, "n must equal the cell count");
@@ -893,6 +852,7 @@ pic_status pic_cell_counts(pic_sim *s, int k, int32_t *out, size_t n) {
 }
 
 pic_status pic_diagnostics(pic_sim *s, pic_diag *out) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     const GridP &g = s->g;
     const double V = s->gd.dx * s->gd.dy * s->gd.dz;

@@ -131,6 +131,8 @@ struct TmaMaps {
 // host-side launch wrappers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
+                               const int *active, const int4 *items, int nitems, cudaStream_t s);
 bool encode_field_maps(const GridP &g, float *const E[2][3], float *const B[2][3],
                        float *const J[3], TmaMaps *maps);
 cudaError_t field_tma_setup();
@@ -138,6 +140,9 @@ size_t field_tma_smem_bytes();
 cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
                              int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
+                                  const int *active, const int2 *items, int nitems, int nctas,
+                                  size_t smem, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm);
 
@@ -155,6 +160,29 @@ cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_d
                                      int *active, int *nactive, int *work, cudaStream_t s);
 cudaError_t launch_cell_histogram(const GridP &g, const SpeciesP &sp, int *counts,
                                   cudaStream_t s);
+
+// batch engine (k_batch.cu)
+struct SortSeg {           // one mobile species of one member
+    SpeciesP src;          // its current buffer (sorted in place)
+    SpeciesP tmp;          // its other buffer, scratch
+    const uint32_t *pid_src;
+    uint32_t *pid_tmp;
+    TileP tp;
+    int *count;            // [ntiles + 1] scratch
+    int *tile_start;       // [ntiles + 1]
+    int *rank;             // this segment's part of the rank scratch
+    long long poff;        // first particle of the segment in the batch index space
+};
+struct SimTiles {          // one member for the active-tile item list
+    int sim, ntiles, nsp, ioff;
+    const int *starts[kMaxSpecies];
+};
+cudaError_t launch_begin_step(int n, const int *member, int *active, int *fpar, long long *done,
+                              const long long *target, long long *const *counters, cudaStream_t s);
+cudaError_t launch_finalize(int n, int *active, int *fpar, long long *done, cudaStream_t s);
+cudaError_t launch_batch_sort(const SortSeg *segs, int nseg, long long total, cudaStream_t s,
+                              int *nlaunch);
+cudaError_t launch_batch_items(const SimTiles *sims, int nsims, int2 *items, cudaStream_t s);
 
 // loader (k_fd.cu)
 struct FDRequest {

@@ -105,6 +105,16 @@ SIGNATURES = {
     "pic_memory_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "pic_last_error": (C.c_char_p, [_H]),
     "pic_cell_counts_noalloc": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int32), C.c_size_t]),
+    "pic_group_create": (C.c_int, [C.c_int, C.c_size_t, C.c_void_p, C.c_int,
+                                   C.POINTER(C.c_void_p)]),
+    "pic_group_destroy": (C.c_int, [_H]),
+    "pic_group_add": (C.c_int, [_H, _H, C.c_int64]),
+    "pic_group_remove": (C.c_int, [_H, _H]),
+    "pic_group_step": (C.c_int, [_H, C.c_int]),
+    "pic_group_sync": (C.c_int, [_H]),
+    "pic_group_progress": (C.c_int, [_H, _H, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pic_group_info": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_size_t),
+                                 C.POINTER(C.c_int64)]),
 }
 PIC_NOALLOC_MAX_CELLS = 1 << 22
 
@@ -335,3 +345,46 @@ def pic_memory_bytes(h):
 def pic_last_error(h=None):
     m = load_library().pic_last_error(h)
     return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# batch engine
+# ---------------------------------------------------------------------------
+
+def pic_group_create(capacity, hbm_budget=0, stream=0, use_graph=1):
+    g = C.c_void_p()
+    _check(load_library().pic_group_create(int(capacity), int(hbm_budget), C.c_void_p(stream),
+                                           int(use_graph), C.byref(g)))
+    return g.value
+
+
+def pic_group_destroy(g):
+    _check(load_library().pic_group_destroy(g))
+
+
+def pic_group_add(g, h, nsteps):
+    _check(load_library().pic_group_add(g, h, int(nsteps)))
+
+
+def pic_group_remove(g, h):
+    _check(load_library().pic_group_remove(g, h))
+
+
+def pic_group_step(g, nsteps):
+    _check(load_library().pic_group_step(g, int(nsteps)))
+
+
+def pic_group_sync(g):
+    _check(load_library().pic_group_sync(g))
+
+
+def pic_group_progress(g, h):
+    d, l = C.c_int64(), C.c_int64()
+    _check(load_library().pic_group_progress(g, h, C.byref(d), C.byref(l)))
+    return d.value, l.value
+
+
+def pic_group_info(g):
+    m, b, n = C.c_int(), C.c_size_t(), C.c_int64()
+    _check(load_library().pic_group_info(g, C.byref(m), C.byref(b), C.byref(n)))
+    return {"members": m.value, "member_bytes": b.value, "launches": n.value}
