@@ -10,6 +10,12 @@ steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+After the timed region the line also carries (rank 0): the end-to-end job
+through the public API with host buffers (e2e), the FP64 oracle on a bounded
+sample (cpu_baseline) with the FP32-vs-FP64 error, the batched sweep of 256
+2D nanostructures against stepping them one by one (batch), and the served
+Poisson job stream against serving the jobs one at a time (serve).
+
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload.  Under torchrun with N > 1
 every rank runs an independent replica (the single simulation has no data
@@ -47,6 +53,13 @@ def parse():
     ap.add_argument("--tile", type=str, default="", help="particle tile, e.g. 8,8,4")
     ap.add_argument("--sort-interval", type=int, default=0)
     ap.add_argument("--tile-order", type=int, default=0)
+    ap.add_argument("--overlap", type=int, default=0, help="1: field update beside the particle phase")
+    ap.add_argument("--particle-ctas", type=int, default=0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--batch-sims", type=int, default=256)
+    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -161,11 +174,12 @@ def field_bytes(wl):
 
 
 def particle_bytes(nfree, nbound, nmat):
-    """Particle kernel: free 3D particle reads cell + 3 offsets + 3 v (28 B),
-    writes 3 offsets + 3 v (24 B); bound reads cell + 3 FP64 anchors + 3
-    displacements + 3 v (52 B), writes displacement + v (24 B); plus E, B
-    read (24 B) and J written (12 B) over the material cells."""
-    return nfree * 52 + nbound * 76 + 36 * nmat
+    """Particle kernel: a free particle reads cell + 3 offsets + 3 v (28 B)
+    and writes 3 offsets + 3 v (24 B); a bound one reads cell + 3 FP32 anchor
+    offsets + 3 displacements + 3 v (40 B) and writes displacement + v
+    (24 B); plus E, B read (24 B) and J read-modify-written (12 B) over the
+    material cells."""
+    return nfree * 52 + nbound * 64 + 36 * nmat
 
 
 def traffic_from_profile(kernel_name, src_file):
@@ -194,20 +208,8 @@ def traffic_from_profile(kernel_name, src_file):
 # ---------------------------------------------------------------------------
 
 def build_sim(pic, I, wl, stream, tuning=None):
-    g = wl["grid"]
-    h = pic.pic_create(pic.make_grid(g["dims"], g["n"], g["d"], g["dt"], bc=g["bc"],
-                                     pml_cells=g["pml_cells"], src=g.get("src")), stream)
-    if tuning:
-        pic.pic_set_tuning(h, **tuning)
-    if wl["mask"] is not None:
-        pic.pic_set_material_mask(h, wl["mask"])
-    for sp in wl["species"]:
-        desc = pic.species_desc(sp["kind"], sp["q"], sp["m"], 0.0, omega0=sp.get("omega0", (0, 0, 0)),
-                                gamma=sp.get("gamma", (0, 0, 0)), v_F=sp.get("v_F", 0.0),
-                                background=sp["background"])
-        pic.pic_load_species(h, desc, density=sp["density"], E_F=sp["E_F"], T=sp["T"],
-                             ppc=sp["ppc"], quiet=sp["quiet"], seed=sp["seed"], stream=sp["stream"])
-    return h
+    from paper_2501_07465_gb300 import runner
+    return runner.make_sim(wl, stream, tuning)
 
 
 def run_gpu(args):
@@ -233,6 +235,10 @@ def run_gpu(args):
         tuning["sort_interval"] = args.sort_interval
     if args.tile_order:
         tuning["tile_order"] = args.tile_order
+    if args.overlap:
+        tuning["overlap"] = args.overlap
+    if args.particle_ctas:
+        tuning["particle_ctas"] = args.particle_ctas
     h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning)
     diag0 = pic.pic_diagnostics(h)
     nparts = sum(diag0["count"])
@@ -296,6 +302,11 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu, fp64 = cpu_baseline_and_error(pic, I, wl, stream)
     pic.pic_destroy(h)
+    batch = serve = None
+    if rank == 0 and not args.no_batch:
+        batch = run_batch_leg(args)
+    if rank == 0 and not args.no_serve:
+        serve = run_serve_leg(args)
 
     launches_per_step = tm["kernel_launches"] / max(args.steps, 1)
     line = {
@@ -305,7 +316,8 @@ def run_gpu(args):
         "config": {"workload": wl["name"], "grid": list(wl["grid"]["n"]),
                    "particles_per_gpu": nparts, "free": nfree, "bound": nbound,
                    "cells": int(np.prod(wl["grid"]["n"])), "material_cells": nmat,
-                   "sort_interval": args.sort_interval or 32, "tile": args.tile or "8,8,8",
+                   "sort_interval": args.sort_interval or 32, "tile": args.tile or "8,8,4",
+                   "overlap": args.overlap, "particle_ctas": args.particle_ctas or "4 per SM",
                    "l2": "inputs larger than L2 (fields 805 MB, no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": kd["name"], "achieved": achieved,
@@ -319,7 +331,7 @@ def run_gpu(args):
                                "sort": tm["sort_ms"]}},
         "bytes_per_particle_step": (fb + pb) / nparts,
         "step_roofline_frac": (fb + pb) * args.steps / (ms / 1e3) / 1e9 / peak,
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_error": fp64,
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_error": fp64, "batch": batch, "serve": serve,
         "clocks": clk.summary(), "gpu_launches": int(tm["kernel_launches"]),
         "gpu_launches_per_step": launches_per_step,
     }
@@ -327,6 +339,43 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_batch_leg(args):
+    """The batched sweep: 256 independent 2D nanostructures stepped to their
+    own step counts by the batch engine (autotuned tile and re-sort interval),
+    against the same simulations stepped one after the other by pic_step."""
+    from paper_2501_07465_gb300 import autotune
+    from paper_2501_07465_gb300 import batch as B
+    from paper_2501_07465_gb300 import inputs as I
+    wls = I.batch2d(count=args.batch_sims)
+    t0 = time.perf_counter()
+    tun, entry = autotune.tune_group(wls)
+    t_tune = time.perf_counter() - t0
+    b = B.run_batch(wls, tuning=tun)
+    s = B.run_serial(wls, tuning=tun)
+    keep = ("seconds", "sims_per_hour", "particle_steps_per_s", "gpu_launches")
+    return {"workload": f"batch2d: {len(wls)} 2D nanostructures (N log-uniform 64-512, disk/rod/"
+                        f"bowtie, 4-16+4-16 ppc, 500-3000 steps)",
+            "sims": len(wls), "particle_steps": b["particle_steps_per_s"] * b["seconds"],
+            "tuning": {"tile": list(tun["tile"]), "sort_interval": tun["sort_interval"],
+                       "cached": entry["cached"], "seconds": t_tune},
+            "batched": {k: b[k] for k in keep}, "serial": {k: s[k] for k in keep},
+            "speedup_vs_serial": s["seconds"] / b["seconds"]}
+
+
+def run_serve_leg(args):
+    """The served stream: Poisson arrivals of mixed 2D / 3D jobs, continuous
+    batching under a 150 GB budget, against the same jobs served one at a
+    time through pic_step."""
+    from paper_2501_07465_gb300 import inputs as I
+    from paper_2501_07465_gb300 import serve as S
+    jobs = I.serve_jobs(args.serve_jobs, args.serve_rate)
+    _, srv = S.serve(jobs, hbm_budget=150e9)
+    _, ser = S.serve_serial(jobs)
+    return {"workload": f"serve_jobs: {len(jobs)} jobs, Poisson {args.serve_rate}/s, 70% 2D "
+                        f"64^2-512^2 / 30% 3D 64^3-192^3, 100-5000 steps",
+            "served": srv, "serial": ser}
 
 
 def run_e2e(pic, I, wl, h_ref, stream, nparts):

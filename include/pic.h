@@ -146,6 +146,10 @@ typedef struct pic_tuning {
     int timing;         /* 1: time every kernel launch with CUDA events [0] */
     int field_plain;    /* 1: field kernel with plain loads even where TMA applies [0] */
     int tile_order;     /* particles inside a tile: 0 spread over cells, 1 cell order [0] */
+    int overlap;        /* 1: the field update runs concurrently with the particle phase
+                           (on a second stream of the handle) and the current is applied
+                           by a short third pass over the field blocks the deposit
+                           touched; 0: particle phase, then the fused field update [0] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */

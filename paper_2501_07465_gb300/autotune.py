@@ -1,0 +1,191 @@
+"""Autotuner for the particle tile and the re-sort interval.
+
+The particle kernel works tile by tile (one persistent CTA takes a tile,
+stages its field box in shared memory and pushes / deposits the particles
+sorted into it), so the tile fixes the particles per CTA and the shared
+memory per CTA; the re-sort interval trades the sort's cost against the
+drift of particles out of their tile.  The best choice depends on the
+grid's dimensionality, the particle density and the structure's size, so it
+is measured: every candidate is built, warmed up and timed with CUDA events
+on the stream it runs on, on a sample of the workloads it is meant for (for a
+batch: a group of the sample, stepped as the batch will be).
+
+Results are cached on disk (JSON; PIC_AUTOTUNE_CACHE or
+~/.cache/paper_2501_07465_gb300/autotune.json) under a key made of the device
+name and a coarse signature of the workload class, so that later runs reuse
+them without timing.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+from . import pic, runner
+
+TILES = {
+    2: [(8, 8, 1), (16, 8, 1), (16, 16, 1), (32, 16, 1), (32, 32, 1)],
+    3: [(8, 8, 4), (8, 8, 8), (16, 8, 4), (8, 4, 4), (16, 16, 4)],
+}
+SORT_INTERVALS = (16, 32, 64)
+
+
+def cache_path():
+    return os.environ.get("PIC_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache",
+                                       "paper_2501_07465_gb300", "autotune.json"))
+
+
+def _load_cache():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(key, entry):
+    data = _load_cache()
+    data[key] = entry
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def signature(workloads):
+    """Coarse class of a set of workloads: dimensionality, log2 of the mean
+    cell count, log2 of the mean particles per cell (rounded)."""
+    dims = workloads[0]["grid"]["dims"]
+    c = sum(runner.cells(w) for w in workloads) / len(workloads)
+    p = sum(runner.particles(w) for w in workloads) / len(workloads)
+    return f"dims{dims}|cells2^{round(math.log2(c))}|ppc2^{round(math.log2(max(p / c, 1e-3)))}"
+
+
+def _device_name():
+    import torch
+    return torch.cuda.get_device_name()
+
+
+def _time_group(workloads, tuning, steps, warm):
+    """ms per group step of `workloads` stepped together with `tuning`."""
+    import torch
+    st = torch.cuda.Stream()
+    hs = []
+    g = pic.pic_group_create(len(workloads), 0, st.cuda_stream, 1)
+    try:
+        for wl in workloads:
+            hs.append(runner.make_sim(wl, 0, tuning))
+            pic.pic_group_add(g, hs[-1], warm + steps)
+        pic.pic_group_step(g, warm)
+        pic.pic_group_sync(g)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        pic.pic_group_step(g, steps)
+        e1.record(st)
+        e1.synchronize()
+        pic.pic_group_sync(g)
+        return e0.elapsed_time(e1) / steps
+    finally:
+        pic.pic_group_destroy(g)
+        for h in hs:
+            pic.pic_destroy(h)
+
+
+def _time_single(wl, tuning, steps, warm):
+    import torch
+    h = runner.make_sim(wl, torch.cuda.current_stream().cuda_stream, tuning)
+    try:
+        st = torch.cuda.current_stream()
+        pic.pic_step(h, warm)
+        pic.pic_sync(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        pic.pic_step(h, steps)
+        e1.record(st)
+        e1.synchronize()
+        pic.pic_sync(h)
+        return e0.elapsed_time(e1) / steps
+    finally:
+        pic.pic_destroy(h)
+
+
+def _search(timer, dims, tiles=None, sort_intervals=SORT_INTERVALS):
+    """Two stages: every tile at the default interval, then every interval
+    at the best tile.  Returns (best tuning, best ms, table)."""
+    table = []
+    best = None
+
+    def timed(tun):
+        try:
+            return timer(tun)
+        except pic.PicError:  # a candidate the library rejects (e.g. shared memory)
+            return math.inf
+
+    for t in tiles or TILES[dims]:
+        tun = dict(tile=t, sort_interval=32)
+        ms = timed(tun)
+        table.append((tun, ms))
+        if best is None or ms < best[1]:
+            best = (tun, ms)
+    for si in sort_intervals:
+        if si == 32:
+            continue
+        tun = dict(tile=best[0]["tile"], sort_interval=si)
+        ms = timed(tun)
+        table.append((tun, ms))
+        if ms < best[1]:
+            best = (tun, ms)
+    return best[0], best[1], table
+
+
+def _entry(best, ms, table, kind, sig):
+    return {"tuning": {"tile": list(best["tile"]), "sort_interval": best["sort_interval"]},
+            "ms_per_step": ms, "kind": kind, "signature": sig,
+            "table": [{"tile": list(t["tile"]), "sort_interval": t["sort_interval"], "ms": m}
+                      for t, m in table]}
+
+
+def _as_tuning(entry):
+    t = entry["tuning"]
+    return {"tile": tuple(t["tile"]), "sort_interval": int(t["sort_interval"])}
+
+
+def tune_group(workloads, sample=16, steps=64, warm=64, use_cache=True, tiles=None):
+    """Best tuning for stepping `workloads` as one group.  Times a group of up
+    to `sample` of them, spread over the size range (sorted by cell count,
+    every k-th).  Returns (tuning dict, cache entry)."""
+    sig = signature(workloads)
+    key = f"{_device_name()}|group|{sig}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return _as_tuning(hit), dict(hit, cached=True)
+    order = sorted(workloads, key=runner.cells)
+    stride = max(1, len(order) // sample)
+    pick = order[::stride][:sample]
+    dims = workloads[0]["grid"]["dims"]
+    best, ms, table = _search(lambda tun: _time_group(pick, tun, steps, warm), dims, tiles)
+    entry = _entry(best, ms, table, "group", sig)
+    entry["sample"] = len(pick)
+    _store_cache(key, entry)
+    return _as_tuning(entry), dict(entry, cached=False)
+
+
+def tune_single(wl, steps=64, warm=64, use_cache=True, tiles=None):
+    """Best tuning for one simulation of workload `wl` stepped alone."""
+    sig = signature([wl])
+    key = f"{_device_name()}|single|{sig}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return _as_tuning(hit), dict(hit, cached=True)
+    best, ms, table = _search(lambda tun: _time_single(wl, tun, steps, warm),
+                              wl["grid"]["dims"], tiles)
+    entry = _entry(best, ms, table, "single", sig)
+    _store_cache(key, entry)
+    return _as_tuning(entry), dict(entry, cached=False)

@@ -152,13 +152,14 @@ __device__ void field_block(const GridP &g, const FieldP &f, const int blk_x, co
     const int kend = DIM == 3 ? min(kbeg + f.zchunk, nz) : 1;
 
     const long long bflag = ((long long)blk_z * f.nby + blk_y) * f.nbx + blk_x;
-    const bool jdirty = f.jdirty[bflag] != 0;
+    const bool jdirty = !f.splitJ && f.jdirty[bflag] != 0;
     __syncthreads();  // every thread has read the flag (cleared at the end)
 
     if (threadIdx.x == 0) {
         double v = 0.0;
         if (f.src_on) {
-            long long n = *f.step_counter - 1;  // the particle phase of step n ran
+            // the particle phase of step n has run (fused step) or runs now (split)
+            long long n = *f.step_counter - (f.splitJ ? 0 : 1);
             double t = ((double)n + 0.5) * f.dt64 - f.src_t0;
             v = f.src_amp * exp(-2.0 * 0.6931471805599453 * t * t / (f.src_tau * f.src_tau)) *
                 sin(f.src_omega * t);
@@ -305,6 +306,34 @@ __global__ void __launch_bounds__(BX * BY)
     field_block<DIM>(sg, sf, w.y, w.z, w.w);
 }
 
+// The current pass of an overlapped step: the field update ran without J
+// (concurrently with the particle phase), so E^{n+1} -= (dt/eps0) J^{n+1/2}
+// here, over the field blocks the deposit flagged; J and the flags are then
+// cleared and the step counter advances.  Same arithmetic as the fused update
+// (E^n + c^2 dt curl B - (dt/eps0) J, one multiply-add per term).
+template <int DIM>
+__global__ void __launch_bounds__(BX * BY) japply_kernel(GridP g, FieldP f, long long *counter) {
+    const long long b = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
+    if (counter && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+        *counter += 1;
+    if (!f.jdirty[b]) return;  // uniform over the CTA
+    const int i = blockIdx.x * BX + threadIdx.x % BX, j = blockIdx.y * BY + threadIdx.x / BX;
+    const int k0 = DIM == 3 ? blockIdx.z * f.zchunk : 0;
+    const int k1 = DIM == 3 ? min(k0 + f.zchunk, g.n[2]) : 1;
+    if (i < g.n[0] && j < g.n[1]) {
+        for (int k = k0; k < k1; ++k) {
+            const long long o = ((long long)k * g.n[1] + j) * g.n[0] + i;
+            for (int c = 0; c < 3; ++c) {
+                const float jc = f.J[c][o];
+                f.En[c][o] = __fmaf_rn(-f.dt_eps0, jc, f.En[c][o]);
+                if (!f.keepJ) f.J[c][o] = 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) f.jdirty_clear[b] = 0;
+}
+
 }  // namespace
 
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
@@ -312,6 +341,13 @@ cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdesc
     if (nitems <= 0) return cudaSuccess;
     if (dims == 3) batch_field_kernel<3><<<nitems, BX * BY, 0, s>>>(grids, fdescs, fpar, active, items);
     else batch_field_kernel<2><<<nitems, BX * BY, 0, s>>>(grids, fdescs, fpar, active, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s) {
+    dim3 grid(f.nbx, f.nby, f.nbz);
+    if (g.dims == 3) japply_kernel<3><<<grid, BX * BY, 0, s>>>(g, f, counter);
+    else japply_kernel<2><<<grid, BX * BY, 0, s>>>(g, f, counter);
     return cudaGetLastError();
 }
 

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT, 4)
     const int kfirst = DIM == 3 ? k0 - 1 : 0;  // first plane loaded
     const int klast = DIM == 3 ? k1 : 0;       // last plane loaded
     const long long bflag = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
-    const bool jdirty = f.jdirty[bflag] != 0;
+    const bool jdirty = !f.splitJ && f.jdirty[bflag] != 0;
     const bool fixx = g.per[0] && (i0 == 0 || i0 + BX >= nx);
     const bool fixy = g.per[1] && (j0 == 0 || j0 + BY >= ny);
 
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NT, 4)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         double v = 0.0;
         if (f.src_on) {
-            long long n = *f.step_counter - 1;
+            long long n = *f.step_counter - (f.splitJ ? 0 : 1);
             double t = ((double)n + 0.5) * f.dt64 - f.src_t0;
             v = f.src_amp * exp(-2.0 * 0.6931471805599453 * t * t / (f.src_tau * f.src_tau)) *
                 sin(f.src_omega * t);

@@ -226,11 +226,11 @@ pic_status sort_all(pic_sim *s, bool include_bound) {
     return PIC_OK;
 }
 
-void record(pic_sim *s, int which, bool start) {
+void record(pic_sim *s, int which, bool start, cudaStream_t on = nullptr) {
     if (!s->tun.timing) return;
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return;
-    cudaEventRecord(e, s->stream);
+    cudaEventRecord(e, on ? on : s->stream);
     (start ? s->ev[which].start : s->ev[which].stop).push_back(e);
 }
 
@@ -464,6 +464,12 @@ pic_status pic_destroy(pic_sim *s) {
     if (!s) return PIC_OK;
     if (s->group) pic_group_remove(s->group, s);
     cudaStreamSynchronize(s->stream);
+    if (s->aux) {
+        cudaStreamSynchronize(s->aux);
+        cudaStreamDestroy(s->aux);
+        cudaEventDestroy(s->ev_fork);
+        cudaEventDestroy(s->ev_join);
+    }
     for (auto &b : s->bufs) {
         if (g_alloc.release) g_alloc.release(b.p, b.bytes, (void *)s->stream, g_alloc.ctx);
         else cudaFree(b.p);
@@ -508,6 +514,7 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     nt.timing = t->timing;
     nt.field_plain = t->field_plain;
     nt.tile_order = t->tile_order;
+    nt.overlap = t->overlap;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;
@@ -737,16 +744,42 @@ pic_status pic_step(pic_sim *s, int nsteps) {
         if (s->tun.keep_J)
             for (int c = 0; c < 3; ++c) CK(s, cudaMemsetAsync(s->J[c], 0, nc * 4, s->stream));
         ParticleLaunch P = particle_params(s);
-        record(s, 0, true);
-        CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
-        record(s, 0, false);
         FieldP f = field_params(s);
-        record(s, 1, true);
-        if (s->use_tma && !s->tun.field_plain)
-            CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
-        else CK(s, launch_field(s->g, f, s->stream));
-        record(s, 1, false);
-        s->launches += 2;
+        const bool tma = s->use_tma && !s->tun.field_plain;
+        if (s->tun.overlap) {
+            // E^n, B^{n-1/2} are only read by both launches and the update
+            // writes the other ping-pong half, so the two can run together;
+            // the current pass after the join adds J and advances the counter
+            if (!s->aux) {
+                CK(s, cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
+                CK(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+                CK(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+            }
+            P.step_counter = nullptr;
+            f.splitJ = 1;
+            CK(s, cudaEventRecord(s->ev_fork, s->stream));
+            record(s, 0, true);
+            CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+            record(s, 0, false);
+            CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+            record(s, 1, true, s->aux);
+            if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->aux));
+            else CK(s, launch_field(s->g, f, s->aux));
+            record(s, 1, false, s->aux);
+            CK(s, cudaEventRecord(s->ev_join, s->aux));
+            CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+            CK(s, launch_japply(s->g, f, s->step_counter, s->stream));
+            s->launches += 3;
+        } else {
+            record(s, 0, true);
+            CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+            record(s, 0, false);
+            record(s, 1, true);
+            if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
+            else CK(s, launch_field(s->g, f, s->stream));
+            record(s, 1, false);
+            s->launches += 2;
+        }
         s->fcur ^= 1;
         s->steps++;
         s->since_sort++;

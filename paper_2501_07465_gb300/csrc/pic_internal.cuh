@@ -86,6 +86,9 @@ struct FieldP {
     float c2dt;          // c^2 dt
     float dt_eps0;       // dt / eps0
     int keepJ;
+    int splitJ;          // 1: J is applied by the separate current pass (overlapped step):
+                         //    the update ignores J and the block flags, and the step
+                         //    counter has not advanced yet when it runs
     int zchunk;
     int nbx, nby, nbz;   // field-block grid (for jdirty)
 };
@@ -131,6 +134,7 @@ struct TmaMaps {
 // host-side launch wrappers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s);
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
                                const int *active, const int4 *items, int nitems, cudaStream_t s);
 bool encode_field_maps(const GridP &g, float *const E[2][3], float *const B[2][3],

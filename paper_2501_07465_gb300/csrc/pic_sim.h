@@ -83,6 +83,10 @@ struct pic_sim {
     long long launches = 0;  // kernels launched by pic_step since the last timing query
     TmaMaps maps;            // TMA descriptors of the field arrays
     bool use_tma = false;    // TMA field kernel (needs nx % 4 == 0)
+    // overlapped step: the field update runs on `aux` while the particle
+    // phase runs on `stream`; fork / join events order them
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace pic {

@@ -21,6 +21,15 @@ Workloads (the paper's metal / graphene settings, Secs. 2-5):
               (v_F = 1e6, n_s = 1e16 m^-2, E_F = 0.2 eV, 300 K), normally
               incident 10 THz pulse of 1e6 V/m, dt = 0.5 dx / (c sqrt 3),
               2000 steps.
+  batch2d     256 independent 2D nanostructures: N x N grids with N drawn
+              log-uniformly in [64, 512], dx = 0.5 nm, CPML min(16, N/8);
+              a disk, rod or bowtie (gap 2-10 nm) holding 4-16 ppc FD free
+              electrons (langmuir2d's n, E_F, T) + as many bound electrons
+              (sphere3d's w0, gamma, N_b = 0.5 n); pulse lambda uniform in
+              400-900 nm; 500-3000 steps each.
+  serve_jobs  a Poisson stream of jobs: 70 % 2D (64^2-512^2), 30 % 3D
+              (64^3-192^3), each taking the species mix of one of the three
+              settings above, 100-5000 steps.
 """
 from __future__ import annotations
 
@@ -216,3 +225,139 @@ def graphene3d(nx=512, ny=512, nz=64, ppc=32, steps=2000, pml=16):
                          ppc=ppc, quiet=0, background=1, seed=SEED_BASE + 2, stream=0)],
         "steps": steps,
     }
+
+
+# ---------------------------------------------------------------------------
+# batched sweep and served job stream
+# ---------------------------------------------------------------------------
+
+def _log_uniform_side(rng, lo, hi, mult=8):
+    n = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+    return int(min(hi, max(lo, mult * round(n / mult))))
+
+
+def _pulse(lam, pml, E0=1e8, fwhm=0.5e-15):
+    return dict(inc_axis=0, pol_axis=1, src_index=pml + 2, E0=E0,
+                omega=2 * math.pi * C_LIGHT / lam, tau=fwhm, t0=1.5 * fwhm)
+
+
+def nanostructure2d(k, N, shape, size_frac, gap_nm, ppc, lam, steps, seed=SEED_BASE + 3):
+    """One 2D nanostructure: N x N cells of 0.5 nm, CPML min(16, N/8) on the
+    four sides, a disk / rod / bowtie mask centred in the box, FD free
+    electrons (n = 8.5e28, E_F = 7.0 eV, 300 K) and bound Lorentz electrons
+    (w0 = 2 pi c / 400 nm, gamma = 1e14, N_b = 0.5 n), ppc of each, a
+    y-polarised pulse entering along x."""
+    dx = 0.5e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(2))
+    pml = min(16, N // 8)
+    L = N - 2 * pml
+    n = (N, N, 1)
+    c = (N / 2, N / 2)
+    if shape == "disk":
+        mask = disk_mask2d(n, c, max(2.0, size_frac * L))
+    elif shape == "rod":
+        mask = rod_mask2d(n, c, max(4.0, 2 * size_frac * L), max(2.0, 0.4 * size_frac * L))
+    else:
+        gap = gap_nm * 1e-9 / dx
+        size = max(3.0, min(size_frac * L, (0.8 * L - gap) / 2))
+        mask = bowtie_mask2d(n, c, size, gap)
+    nfree = 8.5e28
+    w0 = 2 * math.pi * C_LIGHT / 400e-9
+    return {
+        "name": f"nano2d[{k}] {N}^2 {shape} {ppc}+{ppc}ppc",
+        "grid": dict(dims=2, n=n, d=(dx, dx, dx), dt=dt, bc=(1, 1, 0), pml_cells=pml,
+                     src=_pulse(lam, pml)),
+        "mask": mask,
+        "species": [
+            dict(kind=FREE, q=-QE, m=ME, density=nfree, E_F=7.0 * QE, T=300.0, ppc=ppc, quiet=0,
+                 background=1, seed=seed, stream=2 * k),
+            dict(kind=BOUND, q=-QE, m=ME, density=0.5 * nfree, E_F=0.0, T=0.0, ppc=ppc, quiet=0,
+                 background=1, seed=seed, stream=2 * k + 1, omega0=(w0, w0, w0),
+                 gamma=(1e14, 1e14, 1e14)),
+        ],
+        "steps": steps,
+    }
+
+
+def batch2d(count=256, seed=SEED_BASE + 3):
+    """The batched sweep: `count` independent 2D nanostructures (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        N = _log_uniform_side(rng, 64, 512)
+        shape = ("disk", "rod", "bowtie")[int(rng.integers(3))]
+        size_frac = float(rng.uniform(0.15, 0.3))
+        gap_nm = float(rng.uniform(2.0, 10.0))
+        ppc = int(rng.integers(4, 17))
+        lam = float(rng.uniform(400e-9, 900e-9))
+        steps = int(rng.integers(500, 3001))
+        out.append(nanostructure2d(k, N, shape, size_frac, gap_nm, ppc, lam, steps, seed))
+    return out
+
+
+def _periodic_plasma(k, dims, N, steps, seed):
+    """The Langmuir setting's species on an N^dims periodic box (quiet
+    lattice, uniform ions; 16 ppc in 2D, 8 ppc in 3D)."""
+    dx = 0.1e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(dims))
+    ppc = 16 if dims == 2 else 8
+    n = (N, N, 1 if dims == 2 else N)
+    return {
+        "name": f"job[{k}] plasma{dims}d {N}^{dims}",
+        "grid": dict(dims=dims, n=n, d=(dx, dx, dx), dt=dt, bc=(0, 0, 0), pml_cells=0),
+        "mask": None,
+        "species": [dict(kind=FREE, q=-QE, m=ME, density=8.5e28, E_F=7.0 * QE, T=300.0, ppc=ppc,
+                         quiet=1, background=2, seed=seed, stream=k)],
+        "steps": steps,
+    }
+
+
+def _metal3d(k, N, steps, seed):
+    wl = sphere3d(n=N, radius_nm=20.0 * N / 256, pml=min(16, N // 8), steps=steps)
+    wl["name"] = f"job[{k}] metal3d {N}^3"
+    for q, sp in enumerate(wl["species"]):
+        sp["seed"] = seed
+        sp["stream"] = 2 * k + q
+    return wl
+
+
+def _graphene(k, N, steps, seed):
+    nz = max(32, N // 4)
+    wl = graphene3d(nx=N, ny=N, nz=nz, pml=min(16, nz // 4), steps=steps)
+    wl["name"] = f"job[{k}] graphene {N}x{N}x{nz}"
+    wl["species"][0]["seed"] = seed
+    wl["species"][0]["stream"] = k
+    return wl
+
+
+def serve_jobs(count, rate, seed=SEED_BASE + 4):
+    """A seeded Poisson job stream at `rate` jobs/s: 70 % 2D grids (N log-
+    uniform in [64, 512]), 30 % 3D (N in [64, 192]); each job takes the
+    species mix of the Langmuir plasma, the metal nanostructure (free +
+    bound) or, in 3D, the graphene sheet; 100-5000 steps.  Returns the jobs
+    with their arrival times (s) in "arrival"."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        steps = int(rng.integers(100, 5001))
+        if rng.random() < 0.7:
+            N = _log_uniform_side(rng, 64, 512)
+            if rng.random() < 0.5:
+                wl = _periodic_plasma(k, 2, N, steps, seed)
+            else:
+                wl = nanostructure2d(k, N, ("disk", "rod", "bowtie")[int(rng.integers(3))],
+                                     float(rng.uniform(0.15, 0.3)), float(rng.uniform(2, 10)),
+                                     int(rng.integers(4, 17)), float(rng.uniform(400e-9, 900e-9)),
+                                     steps, seed)
+                wl["name"] = f"job[{k}] " + wl["name"]
+        else:
+            N = _log_uniform_side(rng, 64, 192)
+            mix = int(rng.integers(3))
+            wl = (_periodic_plasma(k, 3, N, steps, seed) if mix == 0 else
+                  _metal3d(k, N, steps, seed) if mix == 1 else _graphene(k, N, steps, seed))
+        wl["arrival"] = t
+        wl["job"] = k
+        out.append(wl)
+    return out

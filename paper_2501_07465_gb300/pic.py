@@ -61,7 +61,7 @@ class pic_particles(C.Structure):
 class pic_tuning(C.Structure):
     _fields_ = [("tile", C.c_int * 3), ("sort_interval", C.c_int), ("field_zchunk", C.c_int),
                 ("particle_ctas", C.c_int), ("keep_J", C.c_int), ("timing", C.c_int),
-                ("field_plain", C.c_int), ("tile_order", C.c_int)]
+                ("field_plain", C.c_int), ("tile_order", C.c_int), ("overlap", C.c_int)]
 
 
 class pic_diag(C.Structure):
@@ -254,11 +254,12 @@ def pic_load_species(h, desc: pic_species_desc, cell=None, off=None, v=None, anc
 
 
 def pic_set_tuning(h, tile=(0, 0, 0), sort_interval=0, field_zchunk=0, particle_ctas=0,
-                   keep_J=0, timing=0, field_plain=0, tile_order=0):
+                   keep_J=0, timing=0, field_plain=0, tile_order=0, overlap=0):
     t = pic_tuning()
     t.tile = (C.c_int * 3)(*tile)
     t.sort_interval, t.field_zchunk, t.particle_ctas = sort_interval, field_zchunk, particle_ctas
     t.keep_J, t.timing, t.field_plain, t.tile_order = keep_J, timing, field_plain, tile_order
+    t.overlap = overlap
     _check(load_library().pic_set_tuning(h, C.byref(t)), h)
 
 

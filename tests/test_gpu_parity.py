@@ -59,10 +59,13 @@ def _plane_wave_fields(grid):
 @pytest.mark.parametrize("dims,bc,src", [(3, (0, 0, 0), False), (3, (1, 1, 1), True),
                                          (3, (0, 0, 1), True), (2, (1, 0, 0), True),
                                          (2, (1, 1, 0), False), (2, (0, 0, 0), True)])
-@pytest.mark.parametrize("nx,plain", [(45, 0), (44, 0), (44, 1), (64, 0)])
-def test_field_update_matches_oracle(dims, bc, src, nx, plain):
+@pytest.mark.parametrize("nx,plain,overlap", [(45, 0, 0), (44, 0, 0), (44, 1, 0), (64, 0, 0),
+                                              (44, 0, 1), (45, 0, 1)])
+def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap):
     """nx = 44 and 64 take the TMA-fed kernel (row pitch a multiple of 16 B; 44
-    leaves a ragged last block), nx = 45 and plain = 1 the plain-load one."""
+    leaves a ragged last block), nx = 45 and plain = 1 the plain-load one;
+    overlap = 1 runs the update beside the particle phase with the separate
+    current pass."""
     n = (nx, 20, 36) if dims == 3 else (nx + 25, 41, 1)
     if dims == 2 and nx % 4 == 0:
         n = (nx + 24, 41, 1)
@@ -75,7 +78,7 @@ def test_field_update_matches_oracle(dims, bc, src, nx, plain):
                            omega=2 * np.pi * I.C_LIGHT / 30e-9, tau=4e-17, t0=6e-17)
     fields = _plane_wave_fields(grid)
     pic = _pic()
-    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_plain=plain))
+    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_plain=plain, overlap=overlap))
     s = PR.oracle_sim(grid, None, [], fields=fields)
     try:
         for nsteps, tol in ((1, 1e-5), (99, 1e-3)):
@@ -114,8 +117,8 @@ def _sphere_case(rng, n=(30, 26, 22), radius=8.0, nfree=6000, nbound=4000, bc=(1
     return grid, mask, species
 
 
-@pytest.mark.parametrize("n", [(30, 26, 22), (32, 28, 24)])
-def test_sphere_one_step_particles_fields_counts(n):
+@pytest.mark.parametrize("n,overlap", [((30, 26, 22), 0), ((32, 28, 24), 0), ((32, 28, 24), 1)])
+def test_sphere_one_step_particles_fields_counts(n, overlap):
     rng = np.random.default_rng(11)
     grid, mask, species = _sphere_case(rng, n=n)
     pic = _pic()
@@ -131,7 +134,7 @@ def test_sphere_one_step_particles_fields_counts(n):
                v=species[0]["v"][keep]), species[1]]
     s.close()
     s = PR.oracle_sim(grid, mask, sp)
-    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1))
+    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1, overlap=overlap))
     try:
         pic.pic_step(h, 1)
         s.step(1)
@@ -165,14 +168,14 @@ def test_sphere_one_step_particles_fields_counts(n):
         s.close()
 
 
-@pytest.mark.parametrize("n", [(30, 26, 22), (36, 26, 22)])
-def test_sphere_hundred_steps(n):
+@pytest.mark.parametrize("n,overlap", [((30, 26, 22), 0), ((36, 26, 22), 0), ((36, 26, 22), 1)])
+def test_sphere_hundred_steps(n, overlap):
     rng = np.random.default_rng(12)
     grid, mask, species = _sphere_case(rng, n=n, vscale=1.5e6)
     pic = _pic()
     n = grid["n"]
     s = PR.oracle_sim(grid, mask, species)
-    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16))
+    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16, overlap=overlap))
     try:
         pic.pic_step(h, 100)
         s.step(100)
@@ -194,8 +197,9 @@ def test_sphere_hundred_steps(n):
         s.close()
 
 
-@pytest.mark.parametrize("tile", [(32, 32, 1), (16, 8, 1), (7, 5, 1)])
-def test_free_2d_periodic(tile):
+@pytest.mark.parametrize("tile,overlap", [((32, 32, 1), 0), ((16, 8, 1), 0), ((7, 5, 1), 0),
+                                          ((16, 8, 1), 1)])
+def test_free_2d_periodic(tile, overlap):
     """2D3V periodic plasma, ragged tiles, sorting every 4 steps."""
     rng = np.random.default_rng(21)
     n = (50, 37, 1)
@@ -207,7 +211,7 @@ def test_free_2d_periodic(tile):
     species = [dict(kind=I.FREE, q=-I.QE, m=I.ME, w=w, cell=cell, off=off, v=v, background=2)]
     pic = _pic()
     s = PR.oracle_sim(grid, None, species)
-    h = PR.gpu_sim(grid, None, species, tuning=dict(tile=tile, sort_interval=4))
+    h = PR.gpu_sim(grid, None, species, tuning=dict(tile=tile, sort_interval=4, overlap=overlap))
     try:
         pic.pic_step(h, 1)
         s.step(1)
