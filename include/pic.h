@@ -141,15 +141,21 @@ typedef struct pic_tuning {
     int tile[3];        /* particle tile, cells [8,8,4 in 3D; 32,32,1 in 2D] */
     int sort_interval;  /* steps between tile re-sorts [32] */
     int field_zchunk;   /* z planes per field-kernel CTA [16] */
-    int particle_ctas;  /* persistent particle CTAs [SMs x occupancy] */
+    int particle_ctas;  /* persistent particle CTAs [SMs x occupancy, one CTA per SM
+                           fewer when the field work runs beside the particle phase] */
     int keep_J;         /* 1: J of the last step stays readable (tests) [0] */
     int timing;         /* 1: time every kernel launch with CUDA events [0] */
     int field_plain;    /* 1: field kernel with plain loads even where TMA applies [0] */
     int tile_order;     /* particles inside a tile: 0 spread over cells, 1 cell order [0] */
-    int overlap;        /* 1: the field update runs concurrently with the particle phase
-                           (on a second stream of the handle) and the current is applied
-                           by a short third pass over the field blocks the deposit
-                           touched; 0: particle phase, then the fused field update [0] */
+    int no_overlap;     /* 0: the field work that does not need this step's current runs
+                           beside the particle phase on a second stream of the handle --
+                           the B pass (field_mode 2), or the whole fused update with the
+                           current applied afterwards by a short pass over the field
+                           blocks the deposit touched (field_mode 1); 1: the particle
+                           phase, then the field update, on one stream [0] */
+    int field_mode;     /* 1: fused field update (one pass, 48 B/cell; TMA-fed where nx % 4
+                           == 0); 2: two streaming passes, B then E (36 B/cell each, no
+                           shared memory or barriers); 0: keep the current mode [2] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */
@@ -172,6 +178,8 @@ typedef struct pic_timing {
     double particle_ms, field_ms, sort_ms;       /* summed CUDA-event durations */
     int64_t particle_launches, field_launches, sort_launches;  /* timed phases */
     int64_t kernel_launches;                     /* all kernels pic_step launched */
+    double fieldb_ms;                            /* field_mode 1: the B pass (field_ms: E pass) */
+    int64_t fieldb_launches;
 } pic_timing;
 
 /* Device memory hooks.  alloc returns a device pointer of `bytes` usable on

@@ -140,19 +140,47 @@ __device__ inline float tb(const Stage &s, int c, int lx, int ly) {
     return s.B[c][(ly + 1) * BW + lx + 4];
 }
 
+// CPML position of one column of cells (fixed gi, gj for the whole z march):
+// slab index along x and y (-1 outside) and the offsets of the cell's memory
+// terms in the x-, y- and z-slab arrays for plane 0 / slab plane 0.  The
+// slab arrays are [nz][ny][2P] (x), [nz][2P][nx] (y) and [2P][ny][nx] (z);
+// the host keeps the TMA kernel to grids of fewer than 2^31 cells, so 32-bit
+// offsets suffice.
+struct ColPml {
+    int sx, sy;
+    int ox, oy, oz;
+};
+
+__device__ inline ColPml col_pml(const GridP &g, const FieldP &f, bool valid, int gi, int gj) {
+    ColPml c;
+    const int nx = g.n[0], ny = g.n[1], P = f.P;
+    c.sx = (valid && f.pml[0]) ? slab_idx(gi, nx, P) : -1;
+    c.sy = (valid && f.pml[1]) ? slab_idx(gj, ny, P) : -1;
+    c.ox = gj * (2 * P) + c.sx;
+    c.oy = c.sy * nx + gi;
+    c.oz = gj * nx + gi;
+    return c;
+}
+
+// per-plane strides of the three slab arrays
+struct SlabStride {
+    int x, y, z;
+};
+
 // CPML memory terms of one cell for one plane, loaded together at the start
 // of the plane so that their latencies overlap.  Slot order per axis (see
 // FieldP): x: E_y, E_z, B_y, B_z; y: E_x, E_z, B_x, B_z; z: E_x, E_y, B_x, B_y.
 struct PsiCell {
-    long long idx[3];   // slab index per axis or -1
+    int idx[3];         // offset in the axis' slab arrays, or -1
     float v[3][4];      // psi_in values
 };
 
 template <int DIM>
-__device__ inline void psi_load(const GridP &g, const FieldP &f, int i, int j, int k, PsiCell &pc) {
-    pc.idx[0] = psi_index(g, f, 0, i, j, k);
-    pc.idx[1] = psi_index(g, f, 1, i, j, k);
-    pc.idx[2] = DIM == 3 ? psi_index(g, f, 2, i, j, k) : -1;
+__device__ inline void psi_load(const FieldP &f, const ColPml &cp, int k, int zs,
+                                const SlabStride &st, PsiCell &pc) {
+    pc.idx[0] = cp.sx >= 0 ? cp.ox + k * st.x : -1;
+    pc.idx[1] = cp.sy >= 0 ? cp.oy + k * st.y : -1;
+    pc.idx[2] = (DIM == 3 && zs >= 0) ? cp.oz + zs * st.z : -1;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -169,6 +197,52 @@ __device__ inline float cpml_pre(const FieldP &f, const PsiCell &pc, int a, int 
     float psi = b * pc.v[a][slot] + c * deriv;
     f.psi_out[a][slot][pc.idx[a]] = psi;
     return deriv + psi;
+}
+
+// B^{n+1/2} of a halo cell (low-x column: comps 6, low-y row: comps 5) in a
+// CPML plane: the memory terms are read, not advanced (their own CTA does that)
+template <int DIM>
+__device__ inline void compute_B_halo_pml(const GridP &g, const FieldP &f, const Stage &cur,
+                                          const Stage &nxt, int lx, int ly, int gi, int gj, int k,
+                                          int zs, const ColPml &cp, const SlabStride &st,
+                                          int comps, float *out) {
+    const float dt = g.dt;
+    const int ix = cp.sx >= 0 ? cp.ox + k * st.x : -1;
+    const int iy = cp.sy >= 0 ? cp.oy + k * st.y : -1;
+    const int iz = (DIM == 3 && zs >= 0) ? cp.oz + zs * st.z : -1;
+    auto term = [&](int a, int slot, int idx, int pos, float deriv) {
+        if (idx < 0) return deriv;
+        const float b = __ldg(f.cb_h[a] + pos), c = __ldg(f.ca_h[a] + pos);
+        const float psi = b * __ldg(f.psi_in[a][slot] + idx) + c * deriv;
+        return deriv + psi;
+    };
+    if (comps & 1) {  // B_x
+        float dEz_dy = (te(cur, 2, lx, ly + 1) - te(cur, 2, lx, ly)) * g.inv_d[1];
+        float t1 = term(1, 2, iy, gj, dEz_dy);
+        float t2 = 0.f;
+        if (DIM == 3) {
+            float dEy_dz = (te(nxt, 1, lx, ly) - te(cur, 1, lx, ly)) * g.inv_d[2];
+            t2 = term(2, 2, iz, k, dEy_dz);
+        }
+        out[0] = tb(cur, 0, lx, ly) - dt * (t1 - t2);
+    }
+    if (comps & 2) {  // B_y
+        float t1 = 0.f;
+        if (DIM == 3) {
+            float dEx_dz = (te(nxt, 0, lx, ly) - te(cur, 0, lx, ly)) * g.inv_d[2];
+            t1 = term(2, 3, iz, k, dEx_dz);
+        }
+        float dEz_dx = (te(cur, 2, lx + 1, ly) - te(cur, 2, lx, ly)) * g.inv_d[0];
+        float t2 = term(0, 2, ix, gi, dEz_dx);
+        out[1] = tb(cur, 1, lx, ly) - dt * (t1 - t2);
+    }
+    if (comps & 4) {  // B_z
+        float dEy_dx = (te(cur, 1, lx + 1, ly) - te(cur, 1, lx, ly)) * g.inv_d[0];
+        float dEx_dy = (te(cur, 0, lx, ly + 1) - te(cur, 0, lx, ly)) * g.inv_d[1];
+        float t1 = term(0, 3, ix, gi, dEy_dx);
+        float t2 = term(1, 3, iy, gj, dEx_dy);
+        out[2] = tb(cur, 2, lx, ly) - dt * (t1 - t2);
+    }
 }
 
 // B^{n+1/2} of an own cell in a CPML plane, memory terms preloaded
@@ -280,8 +354,8 @@ __global__ void __launch_bounds__(NT, 4)
     auto zplane = [&](int p) -> int {  // global z of plane p, or -1 outside a wall
         return DIM == 3 ? wrap_or_neg(p, nz, g.per[2]) : 0;
     };
-    auto slot_of = [&](int p) { return (p - kfirst) % S; };
-    auto parity_of = [&](int p) { return (uint32_t)(((p - kfirst) / S) & 1); };
+    auto slot_of = [&](int p) { return (int)((unsigned)(p - kfirst) % S); };  // p >= kfirst
+    auto parity_of = [&](int p) { return ((unsigned)(p - kfirst) / S) & 1u; };
     auto want_B = [&](int p) { return DIM == 2 || p < k1; };
     auto want_J = [&](int p) { return jdirty && (DIM == 2 || (p >= k0 && p < k1)); };
 
@@ -362,11 +436,19 @@ __global__ void __launch_bounds__(NT, 4)
     const bool halo_valid = (halo_col && j0 + hly < ny && hgi >= 0) ||
                             (halo_row && i0 + hlx < nx && hgj >= 0);
 
-    // CTA-uniform: does any cell this CTA reads or writes lie in a CPML slab?
+    // CPML decisions: the halo work takes the CPML path when any cell the CTA
+    // reads lies in an x or y slab (CTA-uniform); an own row (one warp) when
+    // the CTA's columns touch an x slab or the row lies in a y slab; every
+    // plane of a z slab takes it for all.  Cells outside every slab compute
+    // the same values on either path.
     const int P = f.P;
     const bool xyslab = (f.pml[0] && (i0 - 1 < P || i0 + BX > nx - P)) ||
                         (f.pml[1] && (j0 - 1 < P || j0 + BY > ny - P));
-    auto zslab = [&](int k) { return DIM == 3 && f.pml[2] && (k < P || k >= nz - P); };
+    const bool x_own = f.pml[0] && (i0 < P || i0 + BX > nx - P);
+    const bool y_own = f.pml[1] && (j < P || j >= ny - P);  // warp-uniform: j = j0 + warp
+    const ColPml cp_own = col_pml(g, f, own, i, j);
+    const ColPml cp_halo = col_pml(g, f, halo_valid, hgi, hgj);
+    const SlabStride sst{ny * 2 * P, 2 * P * nx, nx * ny};
 
     float Bx_prev = 0.f, By_prev = 0.f;
     bool ok = true;
@@ -411,30 +493,40 @@ __global__ void __launch_bounds__(NT, 4)
         const Stage sc = stage_ptrs(smem, slot_of(k));
         const Stage sn = DIM == 3 ? stage_ptrs(smem, slot_of(k + 1)) : sc;
         const long long o = ((long long)k * ny + j) * nx + i;
-        auto plane = [&](auto pml_tag) {
-            constexpr bool PML = decltype(pml_tag)::value;
-            float bown[3] = {0.f, 0.f, 0.f};
-            PsiCell pc;
-            if (PML && own) psi_load<DIM>(g, f, i, j, k, pc);
+        const int zs = (DIM == 3 && f.pml[2]) ? slab_idx(k, nz, P) : -1;  // uniform
+        const bool own_pml = x_own || y_own || zs >= 0;                     // warp-uniform
+        float bown[3] = {0.f, 0.f, 0.f};
+        PsiCell pc;
+        if (own_pml) {
             if (own) {
-                if (PML) compute_B_own_pml<DIM>(g, f, sc, sn, tx, ty, i, j, k, pc, bown);
-                else compute_B<DIM, false>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
-                f.Bn[0][o] = bown[0];
-                f.Bn[1][o] = bown[1];
-                f.Bn[2][o] = bown[2];
+                psi_load<DIM>(f, cp_own, k, zs, sst, pc);
+                compute_B_own_pml<DIM>(g, f, sc, sn, tx, ty, i, j, k, pc, bown);
             }
-            sB[(0 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[0];
-            sB[(1 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[1];
-            sB[(2 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[2];
-            if (halo_col || halo_row) {
-                float hb[3] = {0.f, 0.f, 0.f};
-                if (halo_valid)
-                    compute_B<DIM, PML>(g, f, sc, sn, hlx, hly, hgi, hgj, k, halo_col ? 6 : 5, false,
-                                        hb);
-                for (int c = 0; c < 3; ++c) sB[(c * (BY + 1) + hly + 1) * (BX + 1) + hlx + 1] = hb[c];
+        } else if (own) {
+            compute_B<DIM, false>(g, f, sc, sn, tx, ty, i, j, k, 7, true, bown);
+        }
+        if (own) {
+            f.Bn[0][o] = bown[0];
+            f.Bn[1][o] = bown[1];
+            f.Bn[2][o] = bown[2];
+        }
+        sB[(0 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[0];
+        sB[(1 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[1];
+        sB[(2 * (BY + 1) + ty + 1) * (BX + 1) + tx + 1] = bown[2];
+        if (halo_col || halo_row) {
+            float hb[3] = {0.f, 0.f, 0.f};
+            if (halo_valid) {
+                if (xyslab || zs >= 0)
+                    compute_B_halo_pml<DIM>(g, f, sc, sn, hlx, hly, hgi, hgj, k, zs, cp_halo, sst,
+                                            halo_col ? 6 : 5, hb);
+                else
+                    compute_B<DIM, false>(g, f, sc, sn, hlx, hly, hgi, hgj, k, halo_col ? 6 : 5,
+                                          false, hb);
             }
-            __syncthreads();  // B: sB of plane k complete
-            if (!own) return;
+            for (int c = 0; c < 3; ++c) sB[(c * (BY + 1) + hly + 1) * (BX + 1) + hlx + 1] = hb[c];
+        }
+        __syncthreads();  // B: sB of plane k complete
+        if (own) {
             auto SB = [&](int c, int ly, int lx) {
                 return sB[(c * (BY + 1) + ly + 1) * (BX + 1) + lx + 1];
             };
@@ -468,7 +560,7 @@ __global__ void __launch_bounds__(NT, 4)
             float tEyx = (bz - SB(2, ty, tx - 1)) * g.inv_d[0];
             float tEzx = (by - SB(1, ty, tx - 1)) * g.inv_d[0];
             float tEzy = (bx - SB(0, ty - 1, tx)) * g.inv_d[1];
-            if (PML) {
+            if (own_pml) {
                 tExy = cpml_pre(f, pc, 1, 0, j, false, tExy);
                 if (DIM == 3) {
                     tExz = cpml_pre(f, pc, 2, 0, k, false, tExz);
@@ -483,9 +575,7 @@ __global__ void __launch_bounds__(NT, 4)
             f.En[2][o] = te(sc, 2, tx, ty) + f.c2dt * (tEzx - tEzy) - f.dt_eps0 * jz;
             Bx_prev = bx;
             By_prev = by;
-        };
-        if (xyslab || zslab(k)) plane(std::true_type{});
-        else plane(std::false_type{});
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

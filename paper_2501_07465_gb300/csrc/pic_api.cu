@@ -121,7 +121,9 @@ pic_status setup_tiles(pic_sim *s) {
     int per_sm = 0;
     CK(s, particle_kernel_setup(dims, s->psmem, &per_sm));
     if (per_sm < 1) return fail(s, PIC_EINVAL, "particle tile does not fit on an SM");
-    s->particle_ctas = s->tun.particle_ctas > 0 ? s->tun.particle_ctas : per_sm * s->num_sms;
+    // beside the field work, one CTA per SM fewer leaves it room (3 of 4 measured best)
+    const int use_sm = (!s->tun.no_overlap && per_sm > 1) ? per_sm - 1 : per_sm;
+    s->particle_ctas = s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm * s->num_sms;
     // tile-indexed buffers
     dfree(s, s->active);
     dfree(s, s->nactive);
@@ -392,6 +394,7 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
     s->tun.tile[1] = d.dims == 3 ? 8 : 32;
     s->tun.tile[2] = d.dims == 3 ? 4 : 1;
     s->tun.sort_interval = 32;
+    s->tun.field_mode = 2;
     s->tun.field_zchunk = 16;
     const long long nc = g.ncell;
     bool ok = true;
@@ -447,8 +450,10 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
         pic_destroy(s);
         return fail(nullptr, st, m);
     }
-    // TMA-fed field kernel where the layout allows it (row pitch a multiple of 16 B)
-    if (encode_field_maps(g, s->E, s->B, s->J, &s->maps) && field_tma_setup() == cudaSuccess)
+    // TMA-fed field kernel where the layout allows it (row pitch a multiple of
+    // 16 B; 32-bit offsets into the CPML slab arrays)
+    if (g.ncell < (1LL << 31) && encode_field_maps(g, s->E, s->B, s->J, &s->maps) &&
+        field_tma_setup() == cudaSuccess)
         s->use_tma = true;
     cudaGetLastError();
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -514,7 +519,8 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     nt.timing = t->timing;
     nt.field_plain = t->field_plain;
     nt.tile_order = t->tile_order;
-    nt.overlap = t->overlap;
+    nt.no_overlap = t->no_overlap;
+    if (t->field_mode == 1 || t->field_mode == 2) nt.field_mode = t->field_mode;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;
@@ -746,15 +752,50 @@ pic_status pic_step(pic_sim *s, int nsteps) {
         ParticleLaunch P = particle_params(s);
         FieldP f = field_params(s);
         const bool tma = s->use_tma && !s->tun.field_plain;
-        if (s->tun.overlap) {
+        if (!s->tun.no_overlap && !s->aux) {
+            CK(s, cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
+            CK(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+            CK(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+        }
+        if (s->tun.field_mode == 2) {
+            if (s->gd.src_on) {  // this step's source current, formed on the host
+                const double t = ((double)s->steps + 0.5) * s->gd.dt - f.src_t0;
+                f.src_val = (float)(f.src_amp * exp(-2.0 * 0.6931471805599453 * t * t /
+                                                    (f.src_tau * f.src_tau)) *
+                                    sin(f.src_omega * t));
+                f.src_host = 1;
+            }
+            // two streaming passes; the B pass reads only E^n, B^{n-1/2} and
+            // writes the other ping-pong half, so with overlap it runs beside
+            // the particle phase
+            if (!s->tun.no_overlap) {
+                CK(s, cudaEventRecord(s->ev_fork, s->stream));
+                record(s, 0, true);
+                CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+                record(s, 0, false);
+                CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+                record(s, 3, true, s->aux);
+                CK(s, launch_field_b(s->g, f, s->aux));
+                record(s, 3, false, s->aux);
+                CK(s, cudaEventRecord(s->ev_join, s->aux));
+                CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+            } else {
+                record(s, 0, true);
+                CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+                record(s, 0, false);
+                record(s, 3, true);
+                CK(s, launch_field_b(s->g, f, s->stream));
+                record(s, 3, false);
+            }
+            record(s, 1, true);
+            CK(s, launch_field_e(s->g, f, s->stream));
+            record(s, 1, false);
+            // each pass is one launch, or two (lean and CPML blocks) with CPML
+            s->launches += 1 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2);
+        } else if (!s->tun.no_overlap) {
             // E^n, B^{n-1/2} are only read by both launches and the update
             // writes the other ping-pong half, so the two can run together;
             // the current pass after the join adds J and advances the counter
-            if (!s->aux) {
-                CK(s, cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
-                CK(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
-                CK(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
-            }
             P.step_counter = nullptr;
             f.splitJ = 1;
             CK(s, cudaEventRecord(s->ev_fork, s->stream));
@@ -936,9 +977,9 @@ pic_status pic_diagnostics(pic_sim *s, pic_diag *out) {
 pic_status pic_get_timing(pic_sim *s, pic_timing *out) {
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     CK(s, cudaStreamSynchronize(s->stream));
-    double ms[3] = {0, 0, 0};
-    int64_t cnt[3] = {0, 0, 0};
-    for (int w = 0; w < 3; ++w) {
+    double ms[4] = {0, 0, 0, 0};
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (int w = 0; w < 4; ++w) {
         TimedEvents &te = s->ev[w];
         for (size_t i = 0; i < te.start.size() && i < te.stop.size(); ++i) {
             float t = 0.f;
@@ -959,6 +1000,8 @@ pic_status pic_get_timing(pic_sim *s, pic_timing *out) {
     out->field_launches = cnt[1];
     out->sort_launches = cnt[2];
     out->kernel_launches = s->launches;
+    out->fieldb_ms = ms[3];
+    out->fieldb_launches = cnt[3];
     s->launches = 0;
     return PIC_OK;
 }

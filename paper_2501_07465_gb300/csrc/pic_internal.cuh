@@ -82,6 +82,8 @@ struct FieldP {
     double src_amp;      // -2 E0 / (eta0 d_inc)
     double src_omega, src_tau, src_t0;
     const long long *step_counter;   // particle phases completed (step n -> n + 1)
+    int src_host;        // 1: src_val holds this step's source current (set by the host)
+    float src_val;
     double dt64;
     float c2dt;          // c^2 dt
     float dt_eps0;       // dt / eps0
@@ -134,6 +136,8 @@ struct TmaMaps {
 // host-side launch wrappers (defined in the kernel translation units)
 // ---------------------------------------------------------------------------
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_field_e(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s);
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
                                const int *active, const int4 *items, int nitems, cudaStream_t s);

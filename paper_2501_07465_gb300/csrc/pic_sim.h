@@ -79,7 +79,7 @@ struct pic_sim {
     int since_sort = 0;
     double omega_p2 = 0.0, omega_b2 = 0.0;
     std::string err;
-    pic::TimedEvents ev[3];  // particle, field, sort
+    pic::TimedEvents ev[4];  // particle, field (E pass), sort, B pass
     long long launches = 0;  // kernels launched by pic_step since the last timing query
     TmaMaps maps;            // TMA descriptors of the field arrays
     bool use_tma = false;    // TMA field kernel (needs nx % 4 == 0)

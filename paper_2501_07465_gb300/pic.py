@@ -61,7 +61,8 @@ class pic_particles(C.Structure):
 class pic_tuning(C.Structure):
     _fields_ = [("tile", C.c_int * 3), ("sort_interval", C.c_int), ("field_zchunk", C.c_int),
                 ("particle_ctas", C.c_int), ("keep_J", C.c_int), ("timing", C.c_int),
-                ("field_plain", C.c_int), ("tile_order", C.c_int), ("overlap", C.c_int)]
+                ("field_plain", C.c_int), ("tile_order", C.c_int), ("no_overlap", C.c_int),
+                ("field_mode", C.c_int)]
 
 
 class pic_diag(C.Structure):
@@ -76,7 +77,8 @@ class pic_diag(C.Structure):
 class pic_timing(C.Structure):
     _fields_ = [("particle_ms", C.c_double), ("field_ms", C.c_double), ("sort_ms", C.c_double),
                 ("particle_launches", C.c_int64), ("field_launches", C.c_int64),
-                ("sort_launches", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("sort_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("fieldb_ms", C.c_double), ("fieldb_launches", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -254,12 +256,13 @@ def pic_load_species(h, desc: pic_species_desc, cell=None, off=None, v=None, anc
 
 
 def pic_set_tuning(h, tile=(0, 0, 0), sort_interval=0, field_zchunk=0, particle_ctas=0,
-                   keep_J=0, timing=0, field_plain=0, tile_order=0, overlap=0):
+                   keep_J=0, timing=0, field_plain=0, tile_order=0, no_overlap=0, field_mode=0):
     t = pic_tuning()
     t.tile = (C.c_int * 3)(*tile)
     t.sort_interval, t.field_zchunk, t.particle_ctas = sort_interval, field_zchunk, particle_ctas
     t.keep_J, t.timing, t.field_plain, t.tile_order = keep_J, timing, field_plain, tile_order
-    t.overlap = overlap
+    t.no_overlap = no_overlap
+    t.field_mode = field_mode  # 0 keeps the current mode
     _check(load_library().pic_set_tuning(h, C.byref(t)), h)
 
 
@@ -334,7 +337,8 @@ def pic_get_timing(h):
     _check(load_library().pic_get_timing(h, C.byref(t)), h)
     return {"particle_ms": t.particle_ms, "field_ms": t.field_ms, "sort_ms": t.sort_ms,
             "particle_launches": t.particle_launches, "field_launches": t.field_launches,
-            "sort_launches": t.sort_launches, "kernel_launches": t.kernel_launches}
+            "sort_launches": t.sort_launches, "kernel_launches": t.kernel_launches,
+            "fieldb_ms": t.fieldb_ms, "fieldb_launches": t.fieldb_launches}
 
 
 def pic_memory_bytes(h):

@@ -59,13 +59,15 @@ def _plane_wave_fields(grid):
 @pytest.mark.parametrize("dims,bc,src", [(3, (0, 0, 0), False), (3, (1, 1, 1), True),
                                          (3, (0, 0, 1), True), (2, (1, 0, 0), True),
                                          (2, (1, 1, 0), False), (2, (0, 0, 0), True)])
-@pytest.mark.parametrize("nx,plain,overlap", [(45, 0, 0), (44, 0, 0), (44, 1, 0), (64, 0, 0),
-                                              (44, 0, 1), (45, 0, 1)])
-def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap):
-    """nx = 44 and 64 take the TMA-fed kernel (row pitch a multiple of 16 B; 44
-    leaves a ragged last block), nx = 45 and plain = 1 the plain-load one;
-    overlap = 1 runs the update beside the particle phase with the separate
-    current pass."""
+@pytest.mark.parametrize("nx,plain,overlap,mode", [
+    (45, 0, 0, 2), (44, 0, 0, 2), (64, 0, 0, 2), (44, 0, 1, 2),
+    (45, 0, 0, 1), (44, 0, 0, 1), (44, 1, 0, 1), (64, 0, 0, 1), (44, 0, 1, 1), (45, 0, 1, 1)])
+def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap, mode):
+    """mode 2: the split B / E passes (overlap = 1: B beside the particle
+    phase).  mode 1, the fused update: nx = 44 and 64 take the TMA-fed kernel
+    (row pitch a multiple of 16 B; 44 leaves a ragged last block), nx = 45 and
+    plain = 1 the plain-load one; overlap = 1 runs it beside the particle phase
+    with the separate current pass."""
     n = (nx, 20, 36) if dims == 3 else (nx + 25, 41, 1)
     if dims == 2 and nx % 4 == 0:
         n = (nx + 24, 41, 1)
@@ -78,7 +80,8 @@ def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap):
                            omega=2 * np.pi * I.C_LIGHT / 30e-9, tau=4e-17, t0=6e-17)
     fields = _plane_wave_fields(grid)
     pic = _pic()
-    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_plain=plain, overlap=overlap))
+    h = PR.gpu_sim(grid, None, [], fields=fields,
+                   tuning=dict(field_plain=plain, no_overlap=1 - overlap, field_mode=mode))
     s = PR.oracle_sim(grid, None, [], fields=fields)
     try:
         for nsteps, tol in ((1, 1e-5), (99, 1e-3)):
@@ -117,8 +120,10 @@ def _sphere_case(rng, n=(30, 26, 22), radius=8.0, nfree=6000, nbound=4000, bc=(1
     return grid, mask, species
 
 
-@pytest.mark.parametrize("n,overlap", [((30, 26, 22), 0), ((32, 28, 24), 0), ((32, 28, 24), 1)])
-def test_sphere_one_step_particles_fields_counts(n, overlap):
+@pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((32, 28, 24), 0, 2),
+                                            ((32, 28, 24), 1, 2), ((32, 28, 24), 0, 1),
+                                            ((32, 28, 24), 1, 1)])
+def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
     rng = np.random.default_rng(11)
     grid, mask, species = _sphere_case(rng, n=n)
     pic = _pic()
@@ -134,7 +139,7 @@ def test_sphere_one_step_particles_fields_counts(n, overlap):
                v=species[0]["v"][keep]), species[1]]
     s.close()
     s = PR.oracle_sim(grid, mask, sp)
-    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1, overlap=overlap))
+    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1, no_overlap=1 - overlap, field_mode=mode))
     try:
         pic.pic_step(h, 1)
         s.step(1)
@@ -168,14 +173,17 @@ def test_sphere_one_step_particles_fields_counts(n, overlap):
         s.close()
 
 
-@pytest.mark.parametrize("n,overlap", [((30, 26, 22), 0), ((36, 26, 22), 0), ((36, 26, 22), 1)])
-def test_sphere_hundred_steps(n, overlap):
+@pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((36, 26, 22), 0, 2),
+                                            ((36, 26, 22), 1, 2), ((36, 26, 22), 0, 1),
+                                            ((36, 26, 22), 1, 1)])
+def test_sphere_hundred_steps(n, overlap, mode):
     rng = np.random.default_rng(12)
     grid, mask, species = _sphere_case(rng, n=n, vscale=1.5e6)
     pic = _pic()
     n = grid["n"]
     s = PR.oracle_sim(grid, mask, species)
-    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16, overlap=overlap))
+    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16, no_overlap=1 - overlap,
+                                                   field_mode=mode))
     try:
         pic.pic_step(h, 100)
         s.step(100)
@@ -197,9 +205,10 @@ def test_sphere_hundred_steps(n, overlap):
         s.close()
 
 
-@pytest.mark.parametrize("tile,overlap", [((32, 32, 1), 0), ((16, 8, 1), 0), ((7, 5, 1), 0),
-                                          ((16, 8, 1), 1)])
-def test_free_2d_periodic(tile, overlap):
+@pytest.mark.parametrize("tile,overlap,mode", [((32, 32, 1), 0, 2), ((16, 8, 1), 0, 2),
+                                               ((7, 5, 1), 0, 2), ((16, 8, 1), 1, 2),
+                                               ((16, 8, 1), 0, 1), ((16, 8, 1), 1, 1)])
+def test_free_2d_periodic(tile, overlap, mode):
     """2D3V periodic plasma, ragged tiles, sorting every 4 steps."""
     rng = np.random.default_rng(21)
     n = (50, 37, 1)
@@ -211,7 +220,8 @@ def test_free_2d_periodic(tile, overlap):
     species = [dict(kind=I.FREE, q=-I.QE, m=I.ME, w=w, cell=cell, off=off, v=v, background=2)]
     pic = _pic()
     s = PR.oracle_sim(grid, None, species)
-    h = PR.gpu_sim(grid, None, species, tuning=dict(tile=tile, sort_interval=4, overlap=overlap))
+    h = PR.gpu_sim(grid, None, species, tuning=dict(tile=tile, sort_interval=4, no_overlap=1 - overlap,
+                                                    field_mode=mode))
     try:
         pic.pic_step(h, 1)
         s.step(1)
