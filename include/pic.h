@@ -183,8 +183,10 @@ typedef struct pic_timing {
 } pic_timing;
 
 /* Device memory hooks.  alloc returns a device pointer of `bytes` usable on
-   `stream` (NULL on failure); free releases it.  Without hooks the library
-   uses cudaMalloc / cudaFree.  Set before creating simulations. */
+   `stream`, aligned to 256 bytes (NULL on failure; a misaligned pointer is
+   handed back to free and the call that needed it fails with PIC_ENOMEM);
+   free releases it.  Without hooks the library uses cudaMalloc / cudaFree.
+   Set before creating simulations. */
 typedef void *(*pic_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*pic_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 pic_status pic_set_allocator(pic_alloc_fn alloc, pic_free_fn release, void *ctx);

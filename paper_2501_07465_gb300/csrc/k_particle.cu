@@ -8,8 +8,9 @@
 // push Sec. 4 Eq. modlorentz and Appendix A.2 (Eqs. modborisvpm,
 // modborisrotsol, modborisBrot); Dirac push Sec. 5; material boundary Sec. 3.
 //
-// Work decomposition: particles are sorted by tile (T0 x T1 x T2 cells).  A
-// persistent CTA takes tiles from the active-tile list; for each tile it
+// Work decomposition: particles are sorted by tile (T0 x T1 x T2 cells).  The
+// persistent CTAs take tiles from the active-tile list (largest particle
+// count first) through an atomic counter as they become free; for each tile it
 // stages E^n and B^{n-1/2} of the tile plus a halo (cells -2 .. T+2 on each
 // axis) in shared memory, turns B^{n-1/2} into B^n = B^{n-1/2} - (dt/2)
 // curl E^n in place, zeroes a J tile of the same extent, and then streams the
@@ -28,7 +29,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kHalo = 2;  // box covers local cells [-2, T+2]
-constexpr int kMaxBlocksPerAxis = 16;  // field blocks a tile box may overlap per axis
 
 __device__ inline float clamp_below_one(float f) {
     return f < 1.0f ? f : 0x1.fffffep-1f;
@@ -172,6 +172,7 @@ __device__ inline void gather(const Acc &A, const int *l, const float *f, float 
     B[1] = interp<DIM>(A, 4, w, true, false, true);
     B[2] = interp<DIM>(A, 5, w, true, true, false);
 }
+
 
 // ---------------------------------------------------------------------------
 // Esirkepov deposit (order 1)
@@ -632,6 +633,30 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, lo
 // the kernel
 // ---------------------------------------------------------------------------
 
+// Box element e -> (bx, by, bz), advanced by the CTA width without divisions.
+struct BoxWalk {
+    int bx, by, bz, e;
+    int dx, dy, dz;  // the step decomposed over the box
+    __device__ inline void start(int b0, int b1, int e0, int step) {
+        const int b01 = b0 * b1;
+        e = e0;
+        bz = e0 / b01;
+        by = (e0 - bz * b01) / b0;
+        bx = e0 - bz * b01 - by * b0;
+        dz = step / b01;
+        dy = (step - dz * b01) / b0;
+        dx = step - dz * b01 - dy * b0;
+    }
+    __device__ inline void next(int b0, int b1, int step) {
+        e += step;
+        bx += dx;
+        by += dy;
+        bz += dz;
+        if (bx >= b0) { bx -= b0; ++by; }
+        if (by >= b1) { by -= b1; ++bz; }
+    }
+};
+
 // One tile of one simulation: stage the field box, push every particle of
 // the tile (all species), flush the J box.  P must live in parameter or shared
 // memory (not global), so that the compiler keeps its fields in registers
@@ -640,11 +665,12 @@ template <int DIM>
 __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, unsigned *s_refl) {
     const TileP &tp = P.tp;
     const int bn = tp.boxn;
+    const int B0 = tp.box[0], B1 = tp.box[1];
     BoxAcc box;
     for (int c = 0; c < 6; ++c) box.F[c] = smem + c * bn;
     for (int c = 0; c < 3; ++c) box.J[c] = smem + (6 + c) * bn;
-    box.b0 = tp.box[0];
-    box.b01 = tp.box[0] * tp.box[1];
+    box.b0 = B0;
+    box.b01 = B0 * B1;
     box.hz = DIM == 3 ? kHalo : 0;
     GlobalAcc<DIM> glob;
     glob.g = &P.g;
@@ -659,48 +685,55 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
     const float hdt = 0.5f * g.dt;
     const int tx = t % tp.nt[0], ty = (t / tp.nt[0]) % tp.nt[1], tz = t / (tp.nt[0] * tp.nt[1]);
     const int org[3] = {tx * tp.T[0], ty * tp.T[1], DIM == 3 ? tz * tp.T[2] : 0};
+    const int step = blockDim.x;
     __syncthreads();  // previous tile's flush is done with the box
     // stage E^n, B^{n-1/2} of the box; zero J
-    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-        bool in = gx >= 0 && gy >= 0 && gz >= 0;
-        long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
-        for (int c = 0; c < 3; ++c) {
-            box.F[c][e] = in ? __ldg(P.E[c] + o) : 0.f;
-            box.F[3 + c][e] = in ? __ldg(P.B[c] + o) : 0.f;
-            box.J[c][e] = 0.f;
+    {
+        BoxWalk w;
+        for (w.start(B0, B1, threadIdx.x, step); w.e < bn; w.next(B0, B1, step)) {
+            int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+            bool in = gx >= 0 && gy >= 0 && gz >= 0;
+            long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                box.F[c][w.e] = in ? __ldg(P.E[c] + o) : 0.f;
+                box.F[3 + c][w.e] = in ? __ldg(P.B[c] + o) : 0.f;
+                box.J[c][w.e] = 0.f;
+            }
         }
     }
     __syncthreads();
     // B^n = B^{n-1/2} - (dt/2) curl E^n (plain Yee curl); zero outside
-    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-        bool hx = bx + 1 < tp.box[0], hy = by + 1 < tp.box[1];
-        bool hz = DIM == 2 || bz + 1 < tp.box[2];
-        if (!(hx && hy && hz)) continue;  // never gathered
-        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-        if (gx < 0 || gy < 0 || gz < 0) {
-            box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
-            continue;
+    {
+        BoxWalk w;
+        for (w.start(B0, B1, threadIdx.x, step); w.e < bn; w.next(B0, B1, step)) {
+            const int e = w.e;
+            const bool hx = w.bx + 1 < B0, hy = w.by + 1 < B1;
+            const bool hz = DIM == 2 || w.bz + 1 < tp.box[2];
+            if (!(hx && hy && hz)) continue;  // never gathered
+            int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+            if (gx < 0 || gy < 0 || gz < 0) {
+                box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
+                continue;
+            }
+            const int sx = 1, sy = box.b0, sz = box.b01;
+            float dEz_dy = (box.F[2][e + sy] - box.F[2][e]) * g.inv_d[1];
+            float dEx_dy = (box.F[0][e + sy] - box.F[0][e]) * g.inv_d[1];
+            float dEz_dx = (box.F[2][e + sx] - box.F[2][e]) * g.inv_d[0];
+            float dEy_dx = (box.F[1][e + sx] - box.F[1][e]) * g.inv_d[0];
+            float dEy_dz = 0.f, dEx_dz = 0.f;
+            if (DIM == 3) {
+                dEy_dz = (box.F[1][e + sz] - box.F[1][e]) * g.inv_d[2];
+                dEx_dz = (box.F[0][e + sz] - box.F[0][e]) * g.inv_d[2];
+            }
+            box.F[3][e] -= hdt * (dEz_dy - dEy_dz);
+            box.F[4][e] -= hdt * (dEx_dz - dEz_dx);
+            box.F[5][e] -= hdt * (dEy_dx - dEx_dy);
         }
-        const int sx = 1, sy = box.b0, sz = box.b01;
-        float dEz_dy = (box.F[2][e + sy] - box.F[2][e]) * g.inv_d[1];
-        float dEx_dy = (box.F[0][e + sy] - box.F[0][e]) * g.inv_d[1];
-        float dEz_dx = (box.F[2][e + sx] - box.F[2][e]) * g.inv_d[0];
-        float dEy_dx = (box.F[1][e + sx] - box.F[1][e]) * g.inv_d[0];
-        float dEy_dz = 0.f, dEx_dz = 0.f;
-        if (DIM == 3) {
-            dEy_dz = (box.F[1][e + sz] - box.F[1][e]) * g.inv_d[2];
-            dEx_dz = (box.F[0][e + sz] - box.F[0][e]) * g.inv_d[2];
-        }
-        box.F[3][e] -= hdt * (dEz_dy - dEy_dz);
-        box.F[4][e] -= hdt * (dEx_dz - dEz_dx);
-        box.F[5][e] -= hdt * (dEy_dx - dEx_dy);
     }
     __syncthreads();
     for (int si = 0; si < P.nsp; ++si) {
@@ -720,43 +753,32 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
         if (r) atomicAdd(&s_refl[si], r);
     }
     __syncthreads();
-    // flush the J tile
-    for (int e = threadIdx.x; e < bn; e += blockDim.x) {
-        int bx = e % tp.box[0], by = (e / tp.box[0]) % tp.box[1], bz = e / box.b01;
-        float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
-        if (jx == 0.f && jy == 0.f && jz == 0.f) continue;
-        int gx = wrap_or_neg(org[0] + bx - kHalo, g.n[0], g.per[0]);
-        int gy = wrap_or_neg(org[1] + by - kHalo, g.n[1], g.per[1]);
-        int gz = DIM == 3 ? wrap_or_neg(org[2] + bz - kHalo, g.n[2], g.per[2]) : 0;
-        if (gx < 0 || gy < 0 || gz < 0) continue;
-        long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
-        if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
-        if (jy != 0.f) atomicAdd(P.J[1] + o, jy);
-        if (jz != 0.f) atomicAdd(P.J[2] + o, jz);
-    }
-    // mark the field blocks the box overlaps
-    if (threadIdx.x == 0) {
-        int bl[3][kMaxBlocksPerAxis], nb[3];
-        const int fb[3] = {kFieldBX, kFieldBY, P.zchunk};
-        for (int ax = 0; ax < 3; ++ax) {
-            nb[ax] = 0;
-            if (ax == 2 && DIM == 2) { bl[2][0] = 0; nb[2] = 1; continue; }
-            for (int c = org[ax] - kHalo; c < org[ax] + tp.T[ax] + kHalo + 1; ++c) {
-                int gc = wrap_or_neg(c, g.n[ax], g.per[ax]);
-                if (gc < 0) continue;
-                int blk = gc / fb[ax];
-                bool seen = false;
-                for (int q = 0; q < nb[ax]; ++q) seen = seen || bl[ax][q] == blk;
-                if (!seen) {
-                    if (nb[ax] < kMaxBlocksPerAxis) bl[ax][nb[ax]++] = blk;
-                    else atomicOr(P.status, kStatusBounds);
+    const int lane = threadIdx.x & 31;
+    // flush the J box; mark the field blocks that received current (lanes of
+    // a warp with the same block elect one to store the flag)
+    BoxWalk w;
+    w.start(B0, B1, threadIdx.x, step);
+    for (int e0 = 0; e0 < bn; e0 += step, w.next(B0, B1, step)) {
+        long long blk = -1;
+        if (w.e < bn) {
+            const int e = w.e;
+            const float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
+            if (jx != 0.f || jy != 0.f || jz != 0.f) {
+                int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
+                int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
+                int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+                if (gx >= 0 && gy >= 0 && gz >= 0) {
+                    const long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
+                    if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
+                    if (jy != 0.f) atomicAdd(P.J[1] + o, jy);
+                    if (jz != 0.f) atomicAdd(P.J[2] + o, jz);
+                    const int bz = DIM == 3 ? gz / P.zchunk : 0;
+                    blk = ((long long)bz * P.nby + gy / kFieldBY) * P.nbx + gx / kFieldBX;
                 }
             }
         }
-        for (int z = 0; z < nb[2]; ++z)
-            for (int y = 0; y < nb[1]; ++y)
-                for (int x = 0; x < nb[0]; ++x)
-                    P.jdirty[((long long)bl[2][z] * P.nby + bl[1][y]) * P.nbx + bl[0][x]] = 1;
+        const unsigned same = __match_any_sync(0xffffffffu, blk);
+        if (blk >= 0 && lane == __ffs(same) - 1) P.jdirty[blk] = 1;
     }
 }
 
@@ -764,13 +786,32 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
+    __shared__ int s_next;
     if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.step_counter) *P.step_counter += 1;
     const int nact = *P.nactive;
-    for (int it = blockIdx.x; it < nact; it += gridDim.x) tile_pass<DIM>(P, P.active[it], smem, s_refl);
+    // take tiles from the list (largest first) as this CTA becomes free; the
+    // read of s_next happens before tile_pass's first barrier, its next write
+    // after tile_pass
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(&P.sched[0], 1);
+        __syncthreads();
+        const int it = s_next;
+        if (it >= nact) break;
+        tile_pass<DIM>(P, P.active[it], smem, s_refl);
+    }
     __syncthreads();
     if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
         atomicAdd(P.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        // the last CTA to finish (every CTA has made its final take) resets
+        // the counters for the next launch
+        __threadfence();
+        if (atomicAdd(&P.sched[1], 1) == (int)gridDim.x - 1) {
+            P.sched[0] = 0;
+            P.sched[1] = 0;
+        }
+    }
 }
 
 // Many simulations in one persistent launch: items[i] = (simulation, tile),

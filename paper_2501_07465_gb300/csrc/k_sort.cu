@@ -5,6 +5,8 @@
 // one CTA of the particle kernel finds the particles of its tile in one
 // contiguous range (tile_start[t] .. tile_start[t+1]).  Order inside a tile
 // is the order in which warps claimed slots (it carries no meaning).
+#include <algorithm>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -134,19 +136,53 @@ __global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_
     }
 }
 
-__global__ void active_flags_kernel(TileP tp, const int *const *starts, int nsp, int *flags) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tp.ntiles; t += gridDim.x * blockDim.x) {
-        int any = 0;
-        for (int s = 0; s < nsp; ++s) any |= (starts[s][t + 1] - starts[s][t]) > 0;
-        flags[t] = any;
+// The active-tile list goes to the particle kernel, whose persistent CTAs
+// take tiles from it in order as they become free: listing the tiles by
+// descending particle count (largest first) evens out the CTAs' loads.  The
+// order is a counting sort over kWorkBuckets count buckets (counts above the
+// last bucket share it).
+constexpr int kWorkBuckets = 8192;
+
+__device__ inline int tile_count(const int *const *starts, int nsp, int t) {
+    int c = 0;
+    for (int s = 0; s < nsp; ++s) c += starts[s][t + 1] - starts[s][t];
+    return c;
+}
+
+__device__ inline int work_key(int count) {  // bucket of a count, largest first
+    return kWorkBuckets - 1 - min(count, kWorkBuckets - 1);
+}
+
+__global__ void active_flags_kernel(TileP tp, const int *const *starts, int nsp, int *flags,
+                                    int *hist) {
+    const int n = max(tp.ntiles, kWorkBuckets + 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (t < tp.ntiles) flags[t] = tile_count(starts, nsp, t) > 0;
+        if (t <= kWorkBuckets) hist[t] = 0;
     }
 }
 
-__global__ void active_scatter_kernel(int ntiles, const int *flags, const int *pos, int *active,
-                                      int *nactive) {
+__global__ void active_scatter_kernel(int ntiles, const int *const *starts, int nsp,
+                                      const int *flags, const int *pos, int *unsorted, int *rank,
+                                      int *hist, int *nactive) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        if (flags[t]) active[pos[t]] = t;
+        if (flags[t]) {
+            const int i = pos[t];
+            unsorted[i] = t;
+            rank[i] = atomicAdd(&hist[work_key(tile_count(starts, nsp, t))], 1);
+        }
         if (t == ntiles - 1) *nactive = pos[ntiles];
+    }
+}
+
+__global__ void active_order_kernel(int ntiles, const int *const *starts, int nsp,
+                                    const int *unsorted, const int *rank, const int *bstart,
+                                    const int *nactive, int *active) {
+    const int n = *nactive;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n && i < ntiles;
+         i += gridDim.x * blockDim.x) {
+        const int t = unsorted[i];
+        active[bstart[work_key(tile_count(starts, nsp, t))] + rank[i]] = t;
     }
 }
 
@@ -231,19 +267,42 @@ cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP 
     return cudaGetLastError();
 }
 
-// flags / positions live in `work`: 2 * (ntiles + 1) + scan_tmp_len(ntiles) ints
+long long active_tiles_work_len(long long ntiles) {
+    return 4 * (ntiles + 1) + 2 * (kWorkBuckets + 1) +
+           std::max(scan_tmp_len(ntiles), scan_tmp_len(kWorkBuckets));
+}
+
+int active_tiles_kernel_count(long long ntiles) {
+    return 3 + scan_kernel_count(ntiles) + scan_kernel_count(kWorkBuckets);
+}
+
+// Scratch in `work` (active_tiles_work_len(ntiles) ints): tile flags, their
+// exclusive scan, the unsorted list, ranks inside a count bucket, the bucket
+// histogram and its scan, the scan's own scratch.
 cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,
                                      int *active, int *nactive, int *work, cudaStream_t s) {
+    const long long nt = tp.ntiles;
     int *flags = work;
-    int *pos = work + tp.ntiles + 1;
-    int *tmp = pos + tp.ntiles + 1;
-    active_flags_kernel<<<grid_for(tp.ntiles, 256), 256, 0, s>>>(tp, starts_dev, nsp, flags);
+    int *pos = flags + nt + 1;
+    int *unsorted = pos + nt + 1;
+    int *rank = unsorted + nt + 1;
+    int *hist = rank + nt + 1;
+    int *bstart = hist + kWorkBuckets + 1;
+    int *tmp = bstart + kWorkBuckets + 1;
+    const int nb = grid_for(std::max<long long>(nt, kWorkBuckets + 1), 256);
+    active_flags_kernel<<<nb, 256, 0, s>>>(tp, starts_dev, nsp, flags, hist);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_scan_int(flags, pos, tp.ntiles, tmp, scan_tmp_len(tp.ntiles), s);
+    e = launch_scan_int(flags, pos, nt, tmp, 0, s);
     if (e != cudaSuccess) return e;
-    active_scatter_kernel<<<grid_for(tp.ntiles, 256), 256, 0, s>>>(tp.ntiles, flags, pos, active,
-                                                                  nactive);
+    active_scatter_kernel<<<grid_for(nt, 256), 256, 0, s>>>(tp.ntiles, starts_dev, nsp, flags, pos,
+                                                           unsorted, rank, hist, nactive);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_scan_int(hist, bstart, kWorkBuckets, tmp, 0, s);
+    if (e != cudaSuccess) return e;
+    active_order_kernel<<<grid_for(nt, 256), 256, 0, s>>>(tp.ntiles, starts_dev, nsp, unsorted, rank,
+                                                         bstart, nactive, active);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,13 @@ void *dalloc(pic_sim *s, size_t bytes) {
         cudaGetLastError();
         p = nullptr;
     }
+    if (p && ((uintptr_t)p & 255u)) {
+        // field arrays feed TMA tensor maps (16-byte aligned at least): a
+        // caller's allocator must align to 256 bytes
+        if (g_alloc.release) g_alloc.release(p, bytes, (void *)s->stream, g_alloc.ctx);
+        s->err = "allocator returned memory not aligned to 256 bytes";
+        p = nullptr;
+    }
     if (p) {
         s->bufs.push_back({p, bytes});
         s->bytes += bytes;
@@ -130,8 +137,10 @@ pic_status setup_tiles(pic_sim *s) {
     dfree(s, s->tile_work);
     dfree(s, s->sort_count);
     const long long nt = tp.ntiles;
-    if (!alloc_zero(s, &s->active, nt + 1) || !alloc_zero(s, &s->nactive, 1) ||
-        !alloc_zero(s, &s->tile_work, 2 * (nt + 1) + scan_tmp_len(nt)) ||
+    // nactive holds the list length, then the particle kernel's tile counter
+    // and finished-CTA count (zero between launches)
+    if (!alloc_zero(s, &s->active, nt + 1) || !alloc_zero(s, &s->nactive, 4) ||
+        !alloc_zero(s, &s->tile_work, active_tiles_work_len(nt)) ||
         !alloc_zero(s, &s->sort_count, nt + 1))
         return fail(s, PIC_ENOMEM, "tile buffers");
     for (int i = 0; i < s->nsp; ++i) {
@@ -214,6 +223,7 @@ pic_status rebuild_active(pic_sim *s) {
     CK(s, cudaStreamSynchronize(s->stream));
     CK(s, launch_active_tiles_work(s->tp, s->starts_dev, s->nsp, s->active, s->nactive,
                                    s->tile_work, s->stream));
+    CK(s, cudaMemsetAsync(s->nactive + 1, 0, 2 * sizeof(int), s->stream));
     return PIC_OK;
 }
 
@@ -299,6 +309,7 @@ ParticleLaunch particle_params(pic_sim *s) {
     P.zchunk = s->tun.field_zchunk;
     P.active = s->active;
     P.nactive = s->nactive;
+    P.sched = s->nactive + 1;
     P.step_counter = s->step_counter;
     P.status = s->status;
     return P;
@@ -744,7 +755,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             // tile_start pointers do not move between sorts: starts_dev stays valid
             CK(s, launch_active_tiles_work(s->tp, s->starts_dev, s->nsp, s->active, s->nactive,
                                            s->tile_work, s->stream));
-            s->launches += 2 + scan_kernel_count(s->tp.ntiles);
+            s->launches += active_tiles_kernel_count(s->tp.ntiles);
             record(s, 2, false);
         }
         if (s->tun.keep_J)

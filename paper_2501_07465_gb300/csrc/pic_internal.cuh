@@ -119,8 +119,9 @@ struct ParticleLaunch {
     const uint8_t *mask;     // may be null (all material)
     uint8_t *jdirty;
     int nbx, nby, nbz, zchunk;
-    const int *active;       // active tile list
+    const int *active;       // active tile list, largest particle count first
     const int *nactive;
+    int *sched;              // [2]: next list entry to take, CTAs finished (reset by the last)
     long long *step_counter;
     int *status;
 };
@@ -164,6 +165,8 @@ int scan_kernel_count(long long n);
 cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
                                 const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
                                 const int *start, const int *rank, bool spread, cudaStream_t s);
+long long active_tiles_work_len(long long ntiles);
+int active_tiles_kernel_count(long long ntiles);
 cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,
                                      int *active, int *nactive, int *work, cudaStream_t s);
 cudaError_t launch_cell_histogram(const GridP &g, const SpeciesP &sp, int *counts,
