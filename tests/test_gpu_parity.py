@@ -481,3 +481,52 @@ def test_bound_only_current_parity():
     finally:
         pic.pic_destroy(h)
         s.close()
+
+
+def test_bound_medium_resonance_and_damping_on_gpu():
+    """A uniform Lorentz medium (periodic, 16 ppc bound electrons at the
+    sphere workload's w0, gamma and N_b = 0.5 n) started from a k-mode
+    displacement rings at w_L = sqrt(w0^2 + w_pb^2 - gamma^2/4) within 1 %
+    and its amplitude decays as exp(-gamma t / 2) within 5 % (Sec. 4, Eq.
+    modlorentz; the dielectric response of Eq. lordielectric)."""
+    nb = 0.5 * 5.9e28
+    nx, ny = 32, 2
+    dx = 0.5e-9
+    dt = 0.5 * dx / (I.C_LIGHT * math.sqrt(2))
+    w0, gam = 4.709e15, 1e14
+    grid = dict(dims=2, n=(nx, ny, 1), d=(dx, dx, dx), dt=dt, bc=(0, 0, 0))
+    cell, off, v = O.fd_load(2, (nx, ny, 1), None, O.KIND_BOUND, I.ME, 0, 0, 0, 16, True, 3, 0)
+    X = I.cell_coords(cell, (nx, ny, 1)) + off
+    k = 2 * math.pi / (nx * dx)
+    D = np.zeros_like(X)
+    D[:, 0] = 1e-12 * np.sin(k * X[:, 0] * dx)
+    w = nb * dx ** 3 / 16
+    species = [dict(kind=I.BOUND, q=-I.QE, m=I.ME, w=w, cell=cell.astype(np.int32),
+                    anchor_off=off.astype(np.float64), disp=D.astype(np.float32),
+                    v=v.astype(np.float32), omega0=(w0,) * 3, gamma=(gam,) * 3, background=1)]
+    i = np.arange(nx)
+    Ex = -nb * (-I.QE) * 1e-12 * np.sin(k * (i + 0.5) * dx) / I.EPS0
+    pic = _pic()
+    h = PR.gpu_sim(grid, None, species, fields={0: np.broadcast_to(Ex, (1, ny, nx)).copy()})
+    wpb2 = nb * I.QE ** 2 / (I.EPS0 * I.ME)
+    wL = math.sqrt(w0 ** 2 + wpb2 - gam ** 2 / 4)
+    nsteps = int(3 * 2 * math.pi / (wL * dt))
+    t, y = [], []
+    try:
+        for it in range(nsteps // 5):
+            pic.pic_step(h, 5)
+            E = pic.pic_read_fields(h, pic.PIC_EX, I.grid_shape(grid["n"]))[0, 0].mean(axis=0)
+            y.append(2 / nx * np.sum(E * np.sin(k * (i + 0.5) * dx)))
+            t.append((it + 1) * 5 * dt)
+    finally:
+        pic.pic_destroy(h)
+    t, y = np.array(t), np.array(y)
+    wfit = _fit_frequency(t, y * np.exp(gam * t / 2), wL)
+    assert abs(wfit / wL - 1) < 0.01
+    A = np.stack([np.cos(wL * t), np.sin(wL * t)], 1)
+    half = len(t) // 2
+    a1 = np.linalg.lstsq(A[:half], y[:half], rcond=None)[0]
+    a2 = np.linalg.lstsq(A[half:], y[half:], rcond=None)[0]
+    ratio = np.linalg.norm(a2) / np.linalg.norm(a1)
+    pred = math.exp(-gam / 2 * (t[half:].mean() - t[:half].mean()))
+    assert abs(ratio / pred - 1) < 0.05
