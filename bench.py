@@ -57,8 +57,9 @@ def parse():
                     help="1: field work beside the particle phase (library default)")
     ap.add_argument("--particle-ctas", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per field CTA")
-    ap.add_argument("--field-mode", type=int, default=2, choices=[1, 2],
-                    help="1: fused field update, 2: split B / E passes")
+    ap.add_argument("--field-mode", type=int, default=2, choices=[1, 2, 3],
+                    help="1: fused field update (shared memory), 2: split B / E passes, "
+                         "3: one streaming pass")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-graphene", action="store_true", help="skip the graphene-sheet leg")
@@ -301,6 +302,9 @@ def run_gpu(args):
                                   src="k_field_split.cu", name="field_e_kernel")
         kernels["field_b"] = dict(bytes=fb_b, ms=avg("fieldb"), total=tm["fieldb_ms"],
                                   src="k_field_split.cu", name="field_b_kernel")
+    elif args.field_mode == 3:
+        kernels["field"] = dict(bytes=fb, ms=avg("field"), total=tm["field_ms"],
+                                src="k_field_stream.cu", name="field_stream_kernel")
     else:
         tma = wl["grid"]["n"][0] % 4 == 0  # the library feeds the fused kernel by TMA then
         kernels["field"] = dict(bytes=fb, ms=avg("field"), total=tm["field_ms"],
@@ -342,7 +346,8 @@ def run_gpu(args):
                    "cells": int(np.prod(wl["grid"]["n"])), "material_cells": nmat,
                    "sort_interval": args.sort_interval or 32, "tile": args.tile or "8,8,4",
                    "overlap": args.overlap, "particle_ctas": args.particle_ctas or ("3 per SM" if args.overlap else "4 per SM"),
-                   "field_mode": "split B/E passes" if split else "fused",
+                   "field_mode": {1: "fused (shared memory)", 2: "split B/E passes",
+                                  3: "one streaming pass"}[args.field_mode],
                    "l2": "inputs larger than L2 (fields 805 MB, no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": kd["name"], "achieved": achieved,
@@ -508,7 +513,7 @@ def run_e2e(pic, I, wl, h_ref, stream, nparts):
                              density=sp["density"])
     pic.pic_step(h, steps)
     diag = pic.pic_diagnostics(h)
-    out.numpy()[...] = pic.pic_read_fields(h, 63, (g["n"][2], g["n"][1], g["n"][0])).ravel()
+    pic.pic_read_fields(h, 63, (g["n"][2], g["n"][1], g["n"][0]), out=out.numpy())
     t1 = time.perf_counter()
     pic.pic_destroy(h)
     return {"value": nparts * steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,

@@ -155,7 +155,9 @@ typedef struct pic_tuning {
                            phase, then the field update, on one stream [0] */
     int field_mode;     /* 1: fused field update (one pass, 48 B/cell; TMA-fed where nx % 4
                            == 0); 2: two streaming passes, B then E (36 B/cell each, no
-                           shared memory or barriers); 0: keep the current mode [2] */
+                           shared memory or barriers); 3: one streaming pass (48 B/cell,
+                           no shared memory or barriers: the -x neighbour's B by warp
+                           shuffle, the -y one recomputed); 0: keep the current mode [2] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */

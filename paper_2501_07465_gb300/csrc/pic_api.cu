@@ -531,7 +531,7 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     nt.field_plain = t->field_plain;
     nt.tile_order = t->tile_order;
     nt.no_overlap = t->no_overlap;
-    if (t->field_mode == 1 || t->field_mode == 2) nt.field_mode = t->field_mode;
+    if (t->field_mode >= 1 && t->field_mode <= 3) nt.field_mode = t->field_mode;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;
@@ -768,14 +768,17 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             CK(s, cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
             CK(s, cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
         }
+        const bool stream = s->tun.field_mode == 3;
+        const int fl = (f.pml[0] || f.pml[1] || f.pml[2]) ? 2 : 1;  // launches of a pass
+        if (s->tun.field_mode != 1 && s->gd.src_on) {
+            // this step's source current, formed on the host
+            const double t = ((double)s->steps + 0.5) * s->gd.dt - f.src_t0;
+            f.src_val = (float)(f.src_amp * exp(-2.0 * 0.6931471805599453 * t * t /
+                                                (f.src_tau * f.src_tau)) *
+                                sin(f.src_omega * t));
+            f.src_host = 1;
+        }
         if (s->tun.field_mode == 2) {
-            if (s->gd.src_on) {  // this step's source current, formed on the host
-                const double t = ((double)s->steps + 0.5) * s->gd.dt - f.src_t0;
-                f.src_val = (float)(f.src_amp * exp(-2.0 * 0.6931471805599453 * t * t /
-                                                    (f.src_tau * f.src_tau)) *
-                                    sin(f.src_omega * t));
-                f.src_host = 1;
-            }
             // two streaming passes; the B pass reads only E^n, B^{n-1/2} and
             // writes the other ping-pong half, so with overlap it runs beside
             // the particle phase
@@ -815,22 +818,24 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             record(s, 0, false);
             CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
             record(s, 1, true, s->aux);
-            if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->aux));
+            if (stream) CK(s, launch_field_stream(s->g, f, s->aux));
+            else if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->aux));
             else CK(s, launch_field(s->g, f, s->aux));
             record(s, 1, false, s->aux);
             CK(s, cudaEventRecord(s->ev_join, s->aux));
             CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
             CK(s, launch_japply(s->g, f, s->step_counter, s->stream));
-            s->launches += 3;
+            s->launches += 2 + (stream ? fl : 1);
         } else {
             record(s, 0, true);
             CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
             record(s, 0, false);
             record(s, 1, true);
-            if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
+            if (stream) CK(s, launch_field_stream(s->g, f, s->stream));
+            else if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
             else CK(s, launch_field(s->g, f, s->stream));
             record(s, 1, false);
-            s->launches += 2;
+            s->launches += 1 + (stream ? fl : 1);
         }
         s->fcur ^= 1;
         s->steps++;

@@ -139,6 +139,7 @@ struct TmaMaps {
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_field_e(const GridP &g, const FieldP &f, cudaStream_t s);
+cudaError_t launch_field_stream(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s);
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
                                const int *active, const int4 *items, int nitems, cudaStream_t s);

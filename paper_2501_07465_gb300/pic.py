@@ -274,12 +274,18 @@ def pic_sync(h):
     _check(load_library().pic_sync(h), h)
 
 
-def pic_read_fields(h, which, shape):
-    """Returns float64 array (ncomp, nz, ny, nx) of the selected components."""
+def pic_read_fields(h, which, shape, out=None):
+    """Returns float64 array (ncomp, nz, ny, nx) of the selected components;
+    `out`, if given, is a C-contiguous float64 array of that many elements
+    (e.g. a view of pinned host memory) that receives them."""
     ncomp = bin(which).count("1")
-    out = np.zeros((ncomp,) + tuple(shape))
+    size = ncomp * int(np.prod(shape))
+    if out is None:
+        out = np.zeros((ncomp,) + tuple(shape))
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != size:
+        raise ValueError("out must be a C-contiguous float64 array of %d elements" % size)
     _check(load_library().pic_read_fields(h, which, _ptr(out, C.c_double), out.size), h)
-    return out
+    return out.reshape((ncomp,) + tuple(shape))
 
 
 def pic_write_fields(h, which, arr):

@@ -61,13 +61,17 @@ def _plane_wave_fields(grid):
                                          (2, (1, 1, 0), False), (2, (0, 0, 0), True)])
 @pytest.mark.parametrize("nx,plain,overlap,mode", [
     (45, 0, 0, 2), (44, 0, 0, 2), (64, 0, 0, 2), (44, 0, 1, 2),
-    (45, 0, 0, 1), (44, 0, 0, 1), (44, 1, 0, 1), (64, 0, 0, 1), (44, 0, 1, 1), (45, 0, 1, 1)])
+    (45, 0, 0, 1), (44, 0, 0, 1), (44, 1, 0, 1), (64, 0, 0, 1), (44, 0, 1, 1), (45, 0, 1, 1),
+    (45, 0, 0, 3), (64, 0, 0, 3), (44, 0, 1, 3), (70, 0, 0, 3)])
 def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap, mode):
     """mode 2: the split B / E passes (overlap = 1: B beside the particle
     phase).  mode 1, the fused update: nx = 44 and 64 take the TMA-fed kernel
     (row pitch a multiple of 16 B; 44 leaves a ragged last block), nx = 45 and
     plain = 1 the plain-load one; overlap = 1 runs it beside the particle phase
-    with the separate current pass."""
+    with the separate current pass.  mode 3, the one-pass streaming update:
+    nx = 45 and 70 leave ragged warps (lane 31 and lane 0 take their x
+    neighbours from memory, beyond-grid lanes only shuffle), overlap = 1 runs
+    it beside the particle phase with the separate current pass."""
     n = (nx, 20, 36) if dims == 3 else (nx + 25, 41, 1)
     if dims == 2 and nx % 4 == 0:
         n = (nx + 24, 41, 1)
@@ -122,7 +126,8 @@ def _sphere_case(rng, n=(30, 26, 22), radius=8.0, nfree=6000, nbound=4000, bc=(1
 
 @pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((32, 28, 24), 0, 2),
                                             ((32, 28, 24), 1, 2), ((32, 28, 24), 0, 1),
-                                            ((32, 28, 24), 1, 1)])
+                                            ((32, 28, 24), 1, 1), ((30, 26, 22), 0, 3),
+                                            ((32, 28, 24), 1, 3)])
 def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
     rng = np.random.default_rng(11)
     grid, mask, species = _sphere_case(rng, n=n)
@@ -175,7 +180,8 @@ def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
 
 @pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((36, 26, 22), 0, 2),
                                             ((36, 26, 22), 1, 2), ((36, 26, 22), 0, 1),
-                                            ((36, 26, 22), 1, 1)])
+                                            ((36, 26, 22), 1, 1), ((36, 26, 22), 0, 3),
+                                            ((36, 26, 22), 1, 3)])
 def test_sphere_hundred_steps(n, overlap, mode):
     rng = np.random.default_rng(12)
     grid, mask, species = _sphere_case(rng, n=n, vscale=1.5e6)
@@ -207,7 +213,8 @@ def test_sphere_hundred_steps(n, overlap, mode):
 
 @pytest.mark.parametrize("tile,overlap,mode", [((32, 32, 1), 0, 2), ((16, 8, 1), 0, 2),
                                                ((7, 5, 1), 0, 2), ((16, 8, 1), 1, 2),
-                                               ((16, 8, 1), 0, 1), ((16, 8, 1), 1, 1)])
+                                               ((16, 8, 1), 0, 1), ((16, 8, 1), 1, 1),
+                                               ((16, 8, 1), 0, 3), ((16, 8, 1), 1, 3)])
 def test_free_2d_periodic(tile, overlap, mode):
     """2D3V periodic plasma, ragged tiles, sorting every 4 steps."""
     rng = np.random.default_rng(21)
