@@ -280,11 +280,12 @@ def run_gpu(args):
     tm = pic.pic_get_timing(h)
     pic.pic_sync(h)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2501_07465_gb300 import replicas
+        ms = replicas.slowest(ms, device="cuda")  # the job ends with the slowest rank
         dist.barrier()
-    total_particles = nparts * world
+    total_particles = nparts
+    if world > 1:
+        total_particles = int(replicas.total(nparts, device="cuda"))
     value = total_particles * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel
@@ -331,8 +332,8 @@ def run_gpu(args):
     batch = serve = graphene = None
     if rank == 0 and not args.no_graphene:
         graphene = run_graphene_leg(args, pic, I, stream, peak)
-    if rank == 0 and not args.no_batch:
-        batch = run_batch_leg(args)
+    if not args.no_batch:
+        batch = run_batch_leg(args, rank, world)
     if rank == 0 and not args.no_serve:
         serve = run_serve_leg(args)
 
@@ -371,26 +372,46 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
 
 
-def run_batch_leg(args):
+def run_batch_leg(args, rank=0, world=1):
     """The batched sweep: 256 independent 2D nanostructures stepped to their
     own step counts by the batch engine (autotuned tile and re-sort interval),
-    against the same simulations stepped one after the other by pic_step."""
+    against the same simulations stepped one after the other by pic_step.
+    With several ranks each takes a share of the sweep (largest cost first,
+    no data exchange); the sweep ends with the slowest rank."""
     from paper_2501_07465_gb300 import autotune
     from paper_2501_07465_gb300 import batch as B
     from paper_2501_07465_gb300 import inputs as I
-    wls = I.batch2d(count=args.batch_sims)
+    from paper_2501_07465_gb300 import replicas
+    wls_all = I.batch2d(count=args.batch_sims)
+    wls = wls_all
+    if world > 1:
+        mine = replicas.shard([replicas.job_cost(w) for w in wls_all], world)[rank]
+        wls = [wls_all[i] for i in mine]
     t0 = time.perf_counter()
     tun, entry = autotune.tune_group(wls)
     t_tune = time.perf_counter() - t0
     b = B.run_batch(wls, tuning=tun)
     s = B.run_serial(wls, tuning=tun)
-    keep = ("seconds", "sims_per_hour", "particle_steps_per_s", "gpu_launches")
-    return {"workload": f"batch2d: {len(wls)} 2D nanostructures (N log-uniform 64-512, disk/rod/"
+    psteps = b["particle_steps_per_s"] * b["seconds"]
+    launches_b, launches_s = b["gpu_launches"], s["gpu_launches"]
+    if world > 1:
+        b["seconds"] = replicas.slowest(b["seconds"], device="cuda")
+        s["seconds"] = replicas.slowest(s["seconds"], device="cuda")
+        psteps = replicas.total(psteps, device="cuda")
+        launches_b = replicas.total(launches_b, device="cuda")
+        launches_s = replicas.total(launches_s, device="cuda")
+    n = len(wls_all)
+
+    def summary(r, launches):
+        return {"seconds": r["seconds"], "sims_per_hour": n / r["seconds"] * 3600,
+                "particle_steps_per_s": psteps / r["seconds"], "gpu_launches": int(launches)}
+
+    return {"workload": f"batch2d: {n} 2D nanostructures (N log-uniform 64-512, disk/rod/"
                         f"bowtie, 4-16+4-16 ppc, 500-3000 steps)",
-            "sims": len(wls), "particle_steps": b["particle_steps_per_s"] * b["seconds"],
+            "sims": n, "ranks": world, "particle_steps": psteps,
             "tuning": {"tile": list(tun["tile"]), "sort_interval": tun["sort_interval"],
                        "cached": entry["cached"], "seconds": t_tune},
-            "batched": {k: b[k] for k in keep}, "serial": {k: s[k] for k in keep},
+            "batched": summary(b, launches_b), "serial": summary(s, launches_s),
             "speedup_vs_serial": s["seconds"] / b["seconds"]}
 
 
