@@ -195,13 +195,16 @@ def particle_bytes(nfree, nbound, nmat):
     return nfree * 52 + nbound * 64 + 36 * nmat
 
 
-def traffic_from_profile(kernel_name, src_file):
+def traffic_from_profile(kernel_name, src_files):
     """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
+    on the current kernel source (the SHA-256 of the source files, joined in
+    order)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_name}_sphere3d.md")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src_file, "rb").read()).hexdigest()
+    if isinstance(src_files, str):
+        src_files = [src_files]
+    sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in src_files)).hexdigest()
     txt = open(path).read()
     got_sha = None
     val = None
@@ -302,7 +305,7 @@ def run_gpu(args):
         kernels["field_e"] = dict(bytes=fb_e, ms=avg("field"), total=tm["field_ms"],
                                   src="k_field_split.cu", name="field_e_kernel")
         kernels["field_b"] = dict(bytes=fb_b, ms=avg("fieldb"), total=tm["fieldb_ms"],
-                                  src="k_field_split.cu", name="field_b_kernel")
+                                  src="k_field_split.cu+k_field_tma.cu", name="field_b_kernel")
     elif args.field_mode == 3:
         kernels["field"] = dict(bytes=fb, ms=avg("field"), total=tm["field_ms"],
                                 src="k_field_stream.cu", name="field_stream_kernel")
@@ -315,7 +318,8 @@ def run_gpu(args):
     kd = kernels[dom]
     achieved = kd["bytes"] / (kd["ms"] / 1e3) / 1e9
     traffic = traffic_from_profile(kd["name"],
-                                   os.path.join(ROOT, "paper_2501_07465_gb300", "csrc", kd["src"]))
+                                   [os.path.join(ROOT, "paper_2501_07465_gb300", "csrc", f)
+                                    for f in kd["src"].split("+")])
     others = {k: {"kernel": v["name"], "bytes_per_launch": v["bytes"], "ms_per_launch": v["ms"],
                   "achieved": v["bytes"] / (v["ms"] / 1e3) / 1e9,
                   "frac": v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak}

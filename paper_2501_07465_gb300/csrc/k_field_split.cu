@@ -139,6 +139,7 @@ __device__ inline float cpml_pre(float *psi_out, int q, float old, float b, floa
 template <int DIM, bool PML>
 __global__ void __launch_bounds__(BX * BY) field_b_kernel(GridP g, FieldP f) {
     if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
+    if (!PML && field_b_tma_block(g, f, blockIdx.x, blockIdx.y, blockIdx.z)) return;  // TMA pass
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int i = blockIdx.x * BX + threadIdx.x % BX;
     const int j = blockIdx.y * BY + threadIdx.x / BX;

@@ -588,6 +588,119 @@ __global__ void __launch_bounds__(NT, 4)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The B pass of the split update, TMA-fed:
+//   B^{n+1/2} = B^{n-1/2} - dt curl E^n
+// on the blocks field_b_tma_block admits (no CPML slab, no halo to wrap).
+// One elected thread streams the planes k0 .. k1 of the E^n tile (40 x 10:
+// the own columns and their +x / +y neighbours) and planes k0 .. k1 - 1 of
+// the B^{n-1/2} tile into a ring of SBP stages; a stage is refilled once every
+// thread has arrived on its "empty" barrier after the plane that reads it
+// last.  The copies in flight wait in shared memory, not in registers, so the
+// pass keeps its bandwidth with one resident CTA per SM, e.g. beside the
+// particle phase.  Every wait is bounded as in the fused kernel.
+// ---------------------------------------------------------------------------
+
+constexpr int SBP = 5;                        // stages
+constexpr int BSTAGE = 3 * (E_PAD + B_PAD);   // bytes per stage
+
+__device__ inline void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(NT) field_b_kernel_tma(GridP g, FieldP f,
+                                                         const __grid_constant__ TmaMaps maps,
+                                                         int cur_buf, int *status) {
+    if (!field_b_tma_block(g, f, blockIdx.x, blockIdx.y, blockIdx.z)) return;  // CTA-uniform
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)SBP * BSTAGE);
+    uint64_t *empty = full + SBP;
+    __shared__ int s_abort;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int k0 = blockIdx.z * f.zchunk, k1 = min(k0 + f.zchunk, nz);
+    const int np = k1 - k0 + 1;  // planes k0 .. k1; the top one for E only
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SBP; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NT);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int p) {  // thread 0 only
+        const int s = p % SBP;
+        int z = k0 + p;
+        if (z >= nz && g.per[2]) z -= nz;  // beyond a wall the box is fill (zero)
+        unsigned char *base = smem + (size_t)s * BSTAGE;
+        const bool wb = p < np - 1;
+        mbar_expect_tx(&full[s], 3 * E_BYTES + (wb ? 3 * B_BYTES : 0));
+        for (int c = 0; c < 3; ++c)
+            tma_load_3d(base + c * E_PAD, &maps.E[cur_buf][c], i0 - 4, j0 - 1, z, &full[s]);
+        if (wb)
+            for (int c = 0; c < 3; ++c)
+                tma_load_3d(base + 3 * E_PAD + c * B_PAD, &maps.B[cur_buf][c], i0 - 4, j0 - 1, z,
+                            &full[s]);
+    };
+    int issued = -1, waited = -1;
+    if (threadIdx.x == 0)
+        for (int p = 0; p < np && p < SBP; ++p) {
+            issue(p);
+            issued = p;
+        }
+    const float dt = g.dt, idx_ = g.inv_d[0], idy = g.inv_d[1], idz = g.inv_d[2];
+    const int e = (ty + 1) * EW + tx + 4, b = (ty + 1) * BW + tx + 4;
+    const long long pl = (long long)nx * ny;
+    long long o = ((long long)k0 * ny + j0 + ty) * nx + i0 + tx;
+    bool ok = mbar_wait(&full[0], 0);
+    if (ok) waited = 0;
+    for (int p = 0; ok && p < np - 1; ++p, o += pl) {
+        const int s = p % SBP, s1 = (p + 1) % SBP;
+        if (!mbar_wait(&full[s1], ((p + 1) / SBP) & 1)) {
+            ok = false;
+            break;
+        }
+        waited = p + 1;
+        const float *E = reinterpret_cast<const float *>(smem + (size_t)s * BSTAGE);
+        const float *Ek = reinterpret_cast<const float *>(smem + (size_t)s1 * BSTAGE);
+        const float *Bt = reinterpret_cast<const float *>(smem + (size_t)s * BSTAGE + 3 * E_PAD);
+        const int ep = E_PAD / 4, bp = B_PAD / 4;  // component stride in floats
+        const float ex = E[e], ey = E[ep + e], ez = E[2 * ep + e];
+        const float dEz_dy = (E[2 * ep + e + EW] - ez) * idy;
+        const float dEx_dy = (E[e + EW] - ex) * idy;
+        const float dEz_dx = (E[2 * ep + e + 1] - ez) * idx_;
+        const float dEy_dx = (E[ep + e + 1] - ey) * idx_;
+        const float dEy_dz = (Ek[ep + e] - ey) * idz;
+        const float dEx_dz = (Ek[e] - ex) * idz;
+        const float bx = Bt[b], by = Bt[bp + b], bz = Bt[2 * bp + b];
+        f.Bn[0][o] = bx - dt * (dEz_dy - dEy_dz);
+        f.Bn[1][o] = by - dt * (dEx_dz - dEz_dx);
+        f.Bn[2][o] = bz - dt * (dEy_dx - dEx_dy);
+        // plane p is the last reader of stage s: release it, refill it
+        mbar_arrive(&empty[s]);
+        if (threadIdx.x == 0 && p + SBP < np) {
+            if (!mbar_wait(&empty[s], (p / SBP) & 1)) {
+                ok = false;
+                s_abort = 1;
+                break;
+            }
+            issue(p + SBP);
+            issued = p + SBP;
+        }
+    }
+    if (!ok) s_abort = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_abort) {
+        atomicOr(status, kStatusTimeout);
+        // let the copies still in flight land before the CTA's memory goes
+        for (int p = waited + 1; p <= issued; ++p) mbar_wait(&full[p % SBP], (p / SBP) & 1);
+    }
+}
+
 }  // namespace
 
 size_t field_tma_smem_bytes() { return (size_t)S * STAGE + SB_BYTES + S * 8 + 128; }
@@ -599,6 +712,16 @@ cudaError_t field_tma_setup() {
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(field_kernel_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)field_tma_smem_bytes());
+}
+
+size_t field_b_tma_smem_bytes() { return (size_t)SBP * BSTAGE + 2 * SBP * 8 + 128; }
+
+cudaError_t launch_field_b_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
+                               int *status, cudaStream_t s) {
+    if (!f.tma_b || g.dims != 3) return cudaSuccess;
+    dim3 grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, (g.n[2] + f.zchunk - 1) / f.zchunk);
+    field_b_kernel_tma<<<grid, NT, field_b_tma_smem_bytes(), s>>>(g, f, maps, cur_buf, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,

@@ -287,6 +287,8 @@ FieldP field_params(pic_sim *s) {
     f.nbx = s->nbx;
     f.nby = s->nby;
     f.nbz = s->nbz;
+    // the split B pass feeds its interior blocks by TMA where the maps exist
+    f.tma_b = (s->tun.field_mode == 2 && s->use_tma && !s->tun.field_plain && s->g.dims == 3) ? 1 : 0;
     return f;
 }
 
@@ -789,6 +791,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
                 record(s, 0, false);
                 CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
                 record(s, 3, true, s->aux);
+                CK(s, launch_field_b_tma(s->g, f, s->maps, s->fcur, s->status, s->aux));
                 CK(s, launch_field_b(s->g, f, s->aux));
                 record(s, 3, false, s->aux);
                 CK(s, cudaEventRecord(s->ev_join, s->aux));
@@ -798,14 +801,16 @@ pic_status pic_step(pic_sim *s, int nsteps) {
                 CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
                 record(s, 0, false);
                 record(s, 3, true);
+                CK(s, launch_field_b_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
                 CK(s, launch_field_b(s->g, f, s->stream));
                 record(s, 3, false);
             }
             record(s, 1, true);
             CK(s, launch_field_e(s->g, f, s->stream));
             record(s, 1, false);
-            // each pass is one launch, or two (lean and CPML blocks) with CPML
-            s->launches += 1 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2);
+            // each pass is one launch, or two (lean and CPML blocks) with CPML,
+            // plus the TMA-fed B pass
+            s->launches += 1 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) + (f.tma_b ? 1 : 0);
         } else if (!s->tun.no_overlap) {
             // E^n, B^{n-1/2} are only read by both launches and the update
             // writes the other ping-pong half, so the two can run together;

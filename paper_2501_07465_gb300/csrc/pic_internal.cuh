@@ -93,9 +93,27 @@ struct FieldP {
                          //    counter has not advanced yet when it runs
     int zchunk;
     int nbx, nby, nbz;   // field-block grid (for jdirty)
+    int tma_b;           // 1: the TMA-fed B pass takes the blocks field_b_tma_block admits
 };
 
 constexpr int kFieldBX = 32, kFieldBY = 8;
+
+// Field blocks (32 x 8 columns x zchunk planes) that the TMA-fed B pass
+// updates when it is on: 3D, no cell in a CPML slab, and the +x / +y
+// neighbour columns inside the grid (no halo to wrap).  The scalar B pass
+// skips exactly these.
+__host__ __device__ inline bool field_b_tma_block(const GridP &g, const FieldP &f, int bx, int by,
+                                                  int bz) {
+    if (!f.tma_b || g.dims != 3) return false;
+    const int i0 = bx * kFieldBX, j0 = by * kFieldBY, k0 = bz * f.zchunk;
+    const int k1 = k0 + f.zchunk < g.n[2] ? k0 + f.zchunk : g.n[2];
+    if (i0 + kFieldBX >= g.n[0] || j0 + kFieldBY >= g.n[1]) return false;
+    const int P = f.P;
+    const bool pml = (f.pml[0] && (i0 < P || i0 + kFieldBX > g.n[0] - P)) ||
+                     (f.pml[1] && (j0 < P || j0 + kFieldBY > g.n[1] - P)) ||
+                     (f.pml[2] && (k0 < P || k1 > g.n[2] - P));
+    return !pml;
+}
 
 // Particle tiling.
 struct TileP {
@@ -147,6 +165,8 @@ bool encode_field_maps(const GridP &g, float *const E[2][3], float *const B[2][3
                        float *const J[3], TmaMaps *maps);
 cudaError_t field_tma_setup();
 size_t field_tma_smem_bytes();
+cudaError_t launch_field_b_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
+                               int *status, cudaStream_t s);
 cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
                              int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);

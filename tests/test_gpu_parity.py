@@ -537,3 +537,39 @@ def test_bound_medium_resonance_and_damping_on_gpu():
     ratio = np.linalg.norm(a2) / np.linalg.norm(a1)
     pred = math.exp(-gam / 2 * (t[half:].mean() - t[:half].mean()))
     assert abs(ratio / pred - 1) < 0.05
+
+
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_tma_b_pass_interior_blocks(overlap):
+    """The split update with the TMA-fed B pass on the interior field blocks
+    (3D, CPML 6 on every face, 96 x 40 x 64 cells: blocks at x 32-63, y 8-31,
+    z 16-31 take it, next to CPML blocks on every side) matches the oracle
+    after 1 and 30 steps and the plain-load path (no TMA) to roundoff."""
+    n = (96, 40, 64)
+    d = (1e-9, 0.8e-9, 1.1e-9)
+    dt = 0.45 * min(d) / (I.C_LIGHT * math.sqrt(3))
+    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(1, 1, 1), pml_cells=6,
+                src=dict(inc_axis=0, pol_axis=1, src_index=9, E0=1e8,
+                         omega=2 * np.pi * I.C_LIGHT / 30e-9, tau=4e-17, t0=6e-17))
+    fields = _plane_wave_fields(grid)
+    pic = _pic()
+    h = PR.gpu_sim(grid, None, [], fields=fields,
+                   tuning=dict(no_overlap=1 - overlap, field_mode=2))
+    hp = PR.gpu_sim(grid, None, [], fields=fields,
+                    tuning=dict(no_overlap=1 - overlap, field_mode=2, field_plain=1))
+    s = PR.oracle_sim(grid, None, [], fields=fields)
+    try:
+        for nsteps, tol in ((1, 1e-5), (29, 1e-4)):
+            pic.pic_step(h, nsteps)
+            pic.pic_step(hp, nsteps)
+            s.step(nsteps)
+            got = PR.gpu_fields(h, grid)
+            plain = PR.gpu_fields(hp, grid)
+            for c in range(6):
+                assert PR.rel_l2(got[c], s.field(c)) < tol, (c, nsteps)
+                assert PR.rel_l2(got[c], plain[c]) < 1e-6, (c, nsteps)
+        pic.pic_sync(h)
+    finally:
+        pic.pic_destroy(h)
+        pic.pic_destroy(hp)
+        s.close()
