@@ -820,16 +820,21 @@ __global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
 template <int DIM>
 __global__ void __launch_bounds__(kThreads)
     batch_particle_kernel(const ParticleLaunch *descs, const int *fpar, const int *active,
-                          const int2 *items, int nitems) {
+                          const int2 *items, int nitems, int *sched) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
     __shared__ ParticleLaunch sP;
-    __shared__ int s_sim;
+    __shared__ int s_sim, s_next;
     if (threadIdx.x == 0) s_sim = -1;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // items are taken through an atomic counter as the CTA becomes free
+    for (;;) {
+        __syncthreads();  // previous item finished with sP / s_refl / s_next
+        if (threadIdx.x == 0) s_next = atomicAdd(&sched[0], 1);
+        __syncthreads();
+        const int it = s_next;
+        if (it >= nitems) break;
         const int2 w = items[it];
         if (w.y < 0 || !active[w.x]) continue;  // uniform over the CTA
-        __syncthreads();  // previous item finished with sP / s_refl
         if (s_sim != w.x) {
             const int *src = reinterpret_cast<const int *>(descs + 2 * w.x + fpar[w.x]);
             int *dst = reinterpret_cast<int *>(&sP);
@@ -843,6 +848,14 @@ __global__ void __launch_bounds__(kThreads)
         __syncthreads();
         if (threadIdx.x < sP.nsp && s_refl[threadIdx.x])
             atomicAdd(sP.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
+    }
+    if (threadIdx.x == 0) {
+        // the last CTA to finish resets the counters for the next launch
+        __threadfence();
+        if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+            sched[0] = 0;
+            sched[1] = 0;
+        }
     }
 }
 
@@ -871,12 +884,15 @@ cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm) {
 }
 
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
-                                  const int *active, const int2 *items, int nitems, int nctas,
-                                  size_t smem, cudaStream_t s) {
+                                  const int *active, const int2 *items, int nitems, int *sched,
+                                  int nctas, size_t smem, cudaStream_t s) {
     if (nctas < 1) nctas = 1;
     if (dims == 3)
-        batch_particle_kernel<3><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems);
-    else batch_particle_kernel<2><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems);
+        batch_particle_kernel<3><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems,
+                                                               sched);
+    else
+        batch_particle_kernel<2><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems,
+                                                               sched);
     return cudaGetLastError();
 }
 

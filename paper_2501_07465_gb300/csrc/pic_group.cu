@@ -48,6 +48,7 @@ struct pic_group {
     long long **counters = nullptr;
     int2 *pitems = nullptr;
     int npitems = 0;
+    int *psched = nullptr;  // particle items: next to take, CTAs finished
     int4 *fitems = nullptr;
     int nfitems = 0;
     SortSeg *segs = nullptr;
@@ -198,11 +199,13 @@ pic_status rebuild(pic_group *g) {
     g->dtarget = galloc<long long>(g, cap);
     g->counters = galloc<long long *>(g, cap);
     g->pitems = galloc<int2>(g, ioff);
+    g->psched = galloc<int>(g, 2);
     g->fitems = galloc<int4>(g, hfitems.size());
     g->segs = galloc<SortSeg>(g, hsegs.size());
     g->simtiles = galloc<SimTiles>(g, hsims.size());
     if (!g->pdesc || !g->grids || !g->fdesc || !g->member || !g->active || !g->fpar || !g->ddone ||
-        !g->dtarget || !g->counters || !g->pitems || !g->fitems || !g->segs || !g->simtiles)
+        !g->dtarget || !g->counters || !g->pitems || !g->psched || !g->fitems || !g->segs ||
+        !g->simtiles)
         return gfail(g, PIC_ENOMEM, "batch tables");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream)
@@ -220,6 +223,7 @@ pic_status rebuild(pic_group *g) {
     GCK(g, up(g->fitems, hfitems.data(), hfitems.size() * sizeof(int4)));
     GCK(g, up(g->segs, hsegs.data(), hsegs.size() * sizeof(SortSeg)));
     GCK(g, up(g->simtiles, hsims.data(), hsims.size() * sizeof(SimTiles)));
+    GCK(g, cudaMemsetAsync(g->psched, 0, 2 * sizeof(int), g->stream));
     GCK(g, cudaStreamSynchronize(g->stream));  // host vectors go out of scope
     g->npitems = ioff;
     g->nfitems = (int)hfitems.size();
@@ -247,7 +251,7 @@ pic_status enqueue_step(pic_group *g) {
     GCK(g, pic::launch_begin_step(g->capacity, g->member, g->active, g->fpar, g->ddone, g->dtarget,
                                   g->counters, g->stream));
     GCK(g, pic::launch_batch_particles(g->dims, g->pdesc, g->fpar, g->active, g->pitems,
-                                       g->npitems, g->pctas, g->psmem, g->stream));
+                                       g->npitems, g->psched, g->pctas, g->psmem, g->stream));
     GCK(g, pic::launch_batch_field(g->dims, g->grids, g->fdesc, g->fpar, g->active, g->fitems,
                                    g->nfitems, g->stream));
     g->launches += 3;

@@ -171,8 +171,8 @@ cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &map
                              int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
-                                  const int *active, const int2 *items, int nitems, int nctas,
-                                  size_t smem, cudaStream_t s);
+                                  const int *active, const int2 *items, int nitems, int *sched,
+                                  int nctas, size_t smem, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm);
 
