@@ -589,13 +589,11 @@ def oracle_setup(I, wl):
 CPU_SAMPLE_STEPS = 2
 
 
-def cpu_baseline_and_error(pic, I, wl_full, stream):
-    """Time the oracle on one host core on the half-scale copy of the
-    workload (128^3 cells, sphere radius 10 nm: the same particle-to-cell
-    ratio, 1/8 of the work per step), CPU_SAMPLE_STEPS steps; compare the
-    GPU's run of the same sample (fresh sim, same seeds) with it."""
-    n = wl_full["grid"]["n"][0] // 2
-    wl = I.sphere3d(n=n, radius_nm=20.0 * n / 256)
+def cpu_baseline_and_error(pic, I, wl, stream):
+    """Time the oracle on one host core on the bench workload itself (the
+    same grid, sphere and particles, loaded by the oracle's own Fermi-Dirac
+    sampler from the same seeds), CPU_SAMPLE_STEPS steps; compare the GPU's
+    run of the same sample (fresh sim, same seeds) with it."""
     t0 = time.perf_counter()
     s = oracle_setup(I, wl)
     t_setup = time.perf_counter() - t0
@@ -638,13 +636,11 @@ def run_reference(args):
     from paper_2501_07465_gb300 import inputs as I
     from oracle import oracle as O
     O.build()
-    # bounded sample: the half-scale copy of the workload (same particle-to-
-    # cell ratio), at most 3 oracle steps
-    n = args.grid // 2
-    wl = I.sphere3d(n=n, radius_nm=20.0 * n / 256)
+    # bounded sample: the GPU arm's workload itself, at most 2 oracle steps
+    wl = I.sphere3d(n=args.grid, radius_nm=20.0 * args.grid / 256)
     s = oracle_setup(I, wl)
     nparts = sum(s.species(k)[0].shape[0] for k in range(s.nsp))
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 2))
     warm = max(0, min(args.warmup, 1))
     s.step(warm)
     t0 = time.perf_counter()
@@ -658,8 +654,8 @@ def run_reference(args):
         "config": {"workload": wl["name"], "grid": list(wl["grid"]["n"]),
                    "particles": nparts, "parallelism": "1 host core"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} steps of {wl['name']}, the half-scale copy of "
-                                   f"the GPU workload (requested {args.steps}, capped at 3)"},
+                         "sample": f"{steps} steps of {wl['name']}, the GPU arm's workload "
+                                   f"(requested {args.steps}, capped at 2)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
