@@ -68,6 +68,7 @@ def _declare(L):
                              C.c_double, C.c_double]
     L.orc_destroy.argtypes = [C.c_void_p]
     L.orc_set_mask.argtypes = [C.c_void_p, _u8p]
+    L.orc_set_permittivity.argtypes = [C.c_void_p, _dp]
     L.orc_add_species.restype = C.c_int
     L.orc_add_species.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                                   _dp, C.c_double, C.c_long, _dp, _dp, _dp, C.c_int]
@@ -241,6 +242,16 @@ class OracleSim:
         m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
         assert m.size == np.prod(self.shape)
         lib().orc_set_mask(self._h, m.ctypes.data_as(_u8p))
+
+    def set_permittivity(self, eps_r):
+        """Relative permittivity per cell, [nz][ny][nx] (None: vacuum)."""
+        if eps_r is None:
+            lib().orc_set_permittivity(self._h, None)
+            return
+        e = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(-1)
+        assert e.size == np.prod(self.shape)
+        self._eps = e
+        lib().orc_set_permittivity(self._h, e.ctypes.data_as(_dp))
 
     def add_species(self, kind, q, m, w, X, V, D=None, omega0=(0, 0, 0), gamma=(0, 0, 0),
                     vF=0.0, bg=0):

@@ -26,8 +26,11 @@
  *      Esirkepov charge-conserving current deposit.
  *   3. Soft plane-wave current sheet added to J.
  *   4. Yee: B^{n+1/2} = B^{n-1/2} - dt (curl E^n + CPML psi),
- *      E^{n+1} = E^n + dt (c^2 (curl B^{n+1/2} + CPML psi) - J / eps0)
- *      (Sec. 4.1 Maxwell curl equations; Eq. consteps with eps = eps0).
+ *      E^{n+1} = E^n + (dt / eps_r) (c^2 (curl B^{n+1/2} + CPML psi) - J / eps0)
+ *      (Sec. 4.1 Maxwell curl equations; Eq. consteps with eps = eps0 eps_r,
+ *      eps_r a per-cell relative permittivity, 1 unless set; E_x at
+ *      (i+1/2, j, k) and the other components of cell (i, j, k) take the
+ *      cell's eps_r).
  *
  * Parity pins: every function below is pinned by a CPU test against a closed
  * form, an invariant or a brute-force check (tests/test_oracle_pins.py).  The
@@ -83,6 +86,7 @@ typedef struct {
     /* CPML coefficients per axis: e = integer positions, h = half positions */
     double *be[3], *ae[3], *bh[3], *ah[3];
     uint8_t *mask;
+    double *eps_r; /* per-cell relative permittivity (NULL: vacuum) */
     double *rho_bg;
     long step;
     int nsp;
@@ -201,7 +205,7 @@ void orc_destroy(void *h) {
         free(s->be[a]); free(s->ae[a]); free(s->bh[a]); free(s->ah[a]);
     }
     for (int k = 0; k < s->nsp; ++k) { free(s->sp[k].X); free(s->sp[k].D); free(s->sp[k].V); }
-    free(s->mask); free(s->rho_bg);
+    free(s->mask); free(s->eps_r); free(s->rho_bg);
     free(s);
 }
 
@@ -209,6 +213,19 @@ void orc_set_mask(void *h, const uint8_t *mask) {
     orc_sim *s = (orc_sim *)h;
     if (!s->mask) s->mask = (uint8_t *)malloc(s->ncell);
     memcpy(s->mask, mask, s->ncell);
+}
+
+/* Relative permittivity per cell (Eq. consteps, eps = eps0 eps_r); NULL
+   restores vacuum. */
+void orc_set_permittivity(void *h, const double *eps_r) {
+    orc_sim *s = (orc_sim *)h;
+    if (!eps_r) {
+        free(s->eps_r);
+        s->eps_r = NULL;
+        return;
+    }
+    if (!s->eps_r) s->eps_r = (double *)malloc(s->ncell * sizeof(double));
+    memcpy(s->eps_r, eps_r, s->ncell * sizeof(double));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -643,9 +660,11 @@ static void yee_update(orc_sim *s) {
                 double tEyx = with_psi(s, 0, s->psiE[0][1], c, s->be[0], s->ae[0], i, dBz_dx);
                 double tEzx = with_psi(s, 0, s->psiE[0][2], c, s->be[0], s->ae[0], i, dBy_dx);
                 double tEzy = with_psi(s, 1, s->psiE[1][2], c, s->be[1], s->ae[1], j, dBx_dy);
-                s->E[0][c] += dt * (c2 * (tExy - tExz) - s->J[0][c] / EPS0);
-                s->E[1][c] += dt * (c2 * (tEyz - tEyx) - s->J[1][c] / EPS0);
-                s->E[2][c] += dt * (c2 * (tEzx - tEzy) - s->J[2][c] / EPS0);
+                /* eps dE/dt = curl H - J (Eq. consteps) */
+                double er = s->eps_r ? s->eps_r[c] : 1.0;
+                s->E[0][c] += dt / er * (c2 * (tExy - tExz) - s->J[0][c] / EPS0);
+                s->E[1][c] += dt / er * (c2 * (tEyz - tEyx) - s->J[1][c] / EPS0);
+                s->E[2][c] += dt / er * (c2 * (tEzx - tEzy) - s->J[2][c] / EPS0);
             }
 }
 
@@ -757,9 +776,17 @@ void orc_cell_counts(void *h, int k, int32_t *out) {
     }
 }
 
+/* eps_r E_a at the E_a node of cell (i, j, k), with the boundary rule of fget */
+static double dget(const orc_sim *s, int a, int i, int j, int k) {
+    int ijk[3] = {i, j, k};
+    if (!wrap_index(s, ijk)) return 0.0;
+    long c = idx3(s, ijk[0], ijk[1], ijk[2]);
+    return (s->eps_r ? s->eps_r[c] : 1.0) * s->E[a][c];
+}
+
 /* out[0..nsp-1]: kinetic energy sum(1/2 m w |v|^2) per species (J);
    out[8]: electric field energy, out[9]: magnetic (B at the half step) (J);
-   out[10]: max |div E - rho/eps0|, out[11]: RMS of the same, out[12]: max |rho/eps0|. */
+   out[10]: max |div (eps_r E) - rho/eps0|, out[11]: RMS of the same, out[12]: max |rho/eps0|. */
 void orc_diag(void *h, double *out) {
     orc_sim *s = (orc_sim *)h;
     for (int k = 0; k < 13; ++k) out[k] = 0.0;
@@ -787,10 +814,11 @@ void orc_diag(void *h, double *out) {
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
                 long c = idx3(s, i, j, k);
-                double div = (fget(s, s->E[0], i, j, k) - fget(s, s->E[0], i - 1, j, k)) / s->d[0] +
-                             (fget(s, s->E[1], i, j, k) - fget(s, s->E[1], i, j - 1, k)) / s->d[1];
+                /* Gauss's law for D = eps0 eps_r E (eps_r 1 in vacuum) */
+                double div = (dget(s, 0, i, j, k) - dget(s, 0, i - 1, j, k)) / s->d[0] +
+                             (dget(s, 1, i, j, k) - dget(s, 1, i, j - 1, k)) / s->d[1];
                 if (s->dims == 3)
-                    div += (fget(s, s->E[2], i, j, k) - fget(s, s->E[2], i, j, k - 1)) / s->d[2];
+                    div += (dget(s, 2, i, j, k) - dget(s, 2, i, j, k - 1)) / s->d[2];
                 double r = div - rho[c] / EPS0;
                 if (fabs(r) > rmax) rmax = fabs(r);
                 rsum += r * r;

@@ -47,6 +47,12 @@ MUTATIONS = [
      "test_dirac_speed_is_vF"),
     ("Philox key increment", "k0 += 0x9E3779B9u;", "k0 += 0x9E3779B7u;",
      "test_philox_known_answers"),
+    ("permittivity on the curl term only",
+     "s->E[1][c] += dt / er * (c2 * (tEyz - tEyx) - s->J[1][c] / EPS0);",
+     "s->E[1][c] += dt * (c2 * (tEyz - tEyx) / er - s->J[1][c] / EPS0);",
+     "test_gauss_law_holds_for_D_in_a_dielectric"),
+    ("permittivity not applied", "double er = s->eps_r ? s->eps_r[c] : 1.0;", "double er = 1.0;",
+     "test_dielectric_half_space_fresnel"),
 ]
 
 

@@ -637,3 +637,69 @@ def test_bound_medium_longitudinal_resonance():
     ratio = np.linalg.norm(a2) / np.linalg.norm(a1)
     pred = math.exp(-gam / 2 * (t[half:].mean() - t[:half].mean()))
     assert abs(ratio / pred - 1) < 0.05
+
+
+def test_dielectric_half_space_fresnel():
+    """Eq. consteps with eps = eps0 eps_r: a plane-wave pulse in vacuum meeting
+    a half-space of eps_r = 4 (n = 2) at normal incidence reflects with
+    r = (1 - n) / (1 + n) = -1/3 and transmits t = 2 / (1 + n) = 2/3 (Fresnel;
+    the medium has no dispersion, so the whole pulse scales by r and t).  The
+    pulse is smooth on the grid (80 cells per wavelength)."""
+    nx = 1200
+    n = (nx, 2, 1)
+    d = (1e-9, 1e-9, 1e-9)
+    dt = 0.5 * 1e-9 / (C * math.sqrt(2))
+    lam = 80e-9
+    tau = 0.25e-15
+    g = dict(dims=2, n=n, d=d, dt=dt, bc=(1, 0, 0), pml_cells=16, src=True, inc_axis=0,
+             pol_axis=1, src_index=40, E0=1e8, omega=2 * math.pi * C / lam, tau=tau,
+             t0=3 * tau)
+    s = O.OracleSim(**g)
+    eps = np.ones((1, 2, nx))
+    eps[..., 700:] = 4.0
+    s.set_permittivity(eps)
+    pa, pb = 200, 800
+    nsteps = int((3 * tau * C / 1e-9 + 1560) / (C * dt / 1e-9))
+    ta, ea, eb = [], [], []
+    for it in range(nsteps):
+        s.step(1)
+        E = s.field(1)[0, 0]
+        ta.append((it + 1) * dt)
+        ea.append(E[pa])
+        eb.append(E[pb])
+    t, ea, eb = np.array(ta), np.abs(ea), np.abs(eb)
+    split = 3 * tau + (pa - 40 + 500) * 1e-9 / C  # between incident and reflected at probe A
+    inc = ea[t < split].max()
+    ref = ea[t > split].max()
+    tra = eb.max()
+    assert abs(ref / inc - 1 / 3) < 0.02 / 3
+    assert abs(tra / inc - 2 / 3) < 0.02 * 2 / 3
+    s.close()
+
+
+def test_gauss_law_holds_for_D_in_a_dielectric():
+    """With a permittivity the step preserves the discrete Gauss law for
+    D = eps0 eps_r E (Eq. consteps): starting neutral (ions at the loaded
+    positions, E = 0), div(eps_r E) - rho/eps0 stays at roundoff while
+    electrons move through and out of a dielectric slab."""
+    rng = np.random.default_rng(17)
+    n = (12, 10, 8)
+    d = (1e-9, 1e-9, 1e-9)
+    dt = 0.5 * 1e-9 / (C * math.sqrt(3))
+    s = O.OracleSim(dims=3, n=n, d=d, dt=dt, bc=(0, 0, 0))
+    eps = np.ones((8, 10, 12))
+    eps[:, :, 4:9] = 3.0
+    s.set_permittivity(eps)
+    npart = 400
+    X = rng.random((npart, 3)) * np.array(n)
+    V = rng.normal(size=(npart, 3)) * 3e6
+    w = 5.9e28 * 1e-27 / 4
+    s.add_species(O.KIND_FREE, -QE, ME, w, X, V, bg=1)
+    qscale = QE * w / 1e-27 / EPS0  # charge density of one macro-particle / eps0
+    assert s.diag()["gauss_max"] < 1e-12 * qscale
+    for _ in range(4):
+        s.step(5)
+        dg = s.diag()
+        assert dg["gauss_max"] < 1e-10 * qscale
+    assert dg["field_E"] > 0
+    s.close()
