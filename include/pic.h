@@ -205,6 +205,18 @@ pic_status pic_destroy(pic_sim *sim);
    Must precede pic_load_species. */
 pic_status pic_set_material_mask(pic_sim *sim, const uint8_t *mask, size_t n);
 
+/* Relative permittivity per cell (Eq. consteps, eps = eps0 eps_r, the
+   material's background response; the bound species add the Lorentz part):
+   the E update becomes E^{n+1} = E^n + (dt / eps_r) (c^2 curl B - J / eps0),
+   each E component taking the eps_r of the cell its node belongs to, and the
+   Gauss residual of pic_diagnostics is taken on D = eps0 eps_r E.  eps_r:
+   n = number of cells values [nz][ny][nx], finite, 1e-6 .. 1e6 (else
+   PIC_EINVAL; the library keeps its own copy of 1 / eps_r); NULL returns to
+   vacuum.  Needs field_mode 2 (PIC_ESTATE otherwise; pic_set_tuning then
+   refuses modes 1 and 3), and such a simulation steps alone (pic_group_add
+   refuses it). */
+pic_status pic_set_permittivity(pic_sim *sim, const float *eps_r, size_t n);
+
 /* Add a species (explicit particles or the Fermi-Dirac loader) and sort it
    into tiles.  Re-checks Eq. dtlimit with the plasma and binding frequencies
    of all species so far (PIC_EDTLIMIT).  *species_id receives its index. */

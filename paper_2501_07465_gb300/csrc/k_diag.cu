@@ -120,17 +120,31 @@ __device__ inline float eget(const GridP &g, const float *F, int i, int j, int k
     return F[((long long)gk * g.n[1] + gj) * g.n[0] + gi];
 }
 
+// eps_r E at the E node of cell (i, j, k) (D / eps0; E beyond a wall is 0)
+__device__ inline double dget(const GridP &g, const float *F, const float *inv_eps, int i, int j,
+                              int k) {
+    int gi = wrap_or_neg(i, g.n[0], g.per[0]);
+    int gj = wrap_or_neg(j, g.n[1], g.per[1]);
+    int gk = g.dims == 3 ? wrap_or_neg(k, g.n[2], g.per[2]) : 0;
+    if (gi < 0 || gj < 0 || gk < 0) return 0.0;
+    const long long c = ((long long)gk * g.n[1] + gj) * g.n[0] + gi;
+    return inv_eps ? (double)F[c] / (double)inv_eps[c] : (double)F[c];
+}
+
+// Gauss's law for D = eps0 eps_r E: div(eps_r E) - rho / eps0
 __global__ void gauss_kernel(GridP g, const float *Ex, const float *Ey, const float *Ez,
-                             const double *rho, const double *rho_bg, DiagAcc *acc) {
+                             const float *inv_eps, const double *rho, const double *rho_bg,
+                             DiagAcc *acc) {
     double rmax = 0.0, rsum = 0.0, qmax = 0.0;
     const double inv_eps0 = 1.0 / kEps0;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell;
          c += (long long)gridDim.x * blockDim.x) {
         int i = (int)(c % g.n[0]), j = (int)((c / g.n[0]) % g.n[1]);
         int k = (int)(c / ((long long)g.n[0] * g.n[1]));
-        double div = ((double)eget(g, Ex, i, j, k) - eget(g, Ex, i - 1, j, k)) / g.d[0] +
-                     ((double)eget(g, Ey, i, j, k) - eget(g, Ey, i, j - 1, k)) / g.d[1];
-        if (g.dims == 3) div += ((double)eget(g, Ez, i, j, k) - eget(g, Ez, i, j, k - 1)) / g.d[2];
+        double div = (dget(g, Ex, inv_eps, i, j, k) - dget(g, Ex, inv_eps, i - 1, j, k)) / g.d[0] +
+                     (dget(g, Ey, inv_eps, i, j, k) - dget(g, Ey, inv_eps, i, j - 1, k)) / g.d[1];
+        if (g.dims == 3)
+            div += (dget(g, Ez, inv_eps, i, j, k) - dget(g, Ez, inv_eps, i, j, k - 1)) / g.d[2];
         double q = (rho[c] + (rho_bg ? rho_bg[c] : 0.0)) * inv_eps0;
         double r = div - q;
         rmax = fmax(rmax, fabs(r));
@@ -218,9 +232,10 @@ cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_ove
     return cudaGetLastError();
 }
 
-cudaError_t launch_gauss(const GridP &g, const float *const *E, const double *rho,
-                         const double *rho_bg, DiagAcc *acc, cudaStream_t s) {
-    gauss_kernel<<<blocks_for(g.ncell), 256, 0, s>>>(g, E[0], E[1], E[2], rho, rho_bg, acc);
+cudaError_t launch_gauss(const GridP &g, const float *const *E, const float *inv_eps,
+                         const double *rho, const double *rho_bg, DiagAcc *acc, cudaStream_t s) {
+    gauss_kernel<<<blocks_for(g.ncell), 256, 0, s>>>(g, E[0], E[1], E[2], inv_eps, rho, rho_bg,
+                                                     acc);
     return cudaGetLastError();
 }
 

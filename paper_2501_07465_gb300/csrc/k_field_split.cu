@@ -210,11 +210,12 @@ __global__ void __launch_bounds__(BX * BY) field_b_kernel(GridP g, FieldP f) {
 // and in CPML blocks the two E memory terms per slab axis
 struct ELoads {
     float bx, by, bz, bz_y, bx_y, bz_x, by_x, e0, e1, e2, jx, jy, jz;
+    float ie;  // 1 / eps_r of the cell
     float px[2], py[2], pz[2];
     int qx, qy, qz;
 };
 
-template <int DIM, bool PML>
+template <int DIM, bool PML, bool EPS>
 __device__ inline void e_loads(const GridP &g, const FieldP &f, const ColSlab &cs, long long o,
                                int k, long long dym, int dxm, bool hx, bool hy, bool jdirty,
                                ELoads &L) {
@@ -228,6 +229,7 @@ __device__ inline void e_loads(const GridP &g, const FieldP &f, const ColSlab &c
     L.e0 = __ldg(f.E[0] + o);
     L.e1 = __ldg(f.E[1] + o);
     L.e2 = __ldg(f.E[2] + o);
+    L.ie = EPS ? __ldg(f.inv_eps + o) : 1.f;
     L.jx = L.jy = L.jz = 0.f;
     if (jdirty) {  // J is cleared by this thread one plane later
         L.jx = __ldcg(f.J[0] + o);
@@ -262,7 +264,9 @@ __device__ inline float source_value(const FieldP &f) {
                    sin(f.src_omega * t));
 }
 
-template <int DIM, bool PML>
+// EPS: a permittivity is set (its own instantiation: the vacuum kernel keeps
+// its registers)
+template <int DIM, bool PML, bool EPS>
 __global__ void __launch_bounds__(BX * BY) field_e_kernel(GridP g, FieldP f) {
     if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
     __shared__ float s_src;
@@ -313,9 +317,10 @@ __global__ void __launch_bounds__(BX * BY) field_e_kernel(GridP g, FieldP f) {
             bym = __ldg(f.Bn[1] + om);
         }
         ELoads cur, nxt;
-        e_loads<DIM, PML>(g, f, cs, o, k0, dym, dxm, hx, hy, jdirty, cur);
+        e_loads<DIM, PML, EPS>(g, f, cs, o, k0, dym, dxm, hx, hy, jdirty, cur);
         for (int k = k0; k < k1; ++k, o += pl) {
-            if (k + 1 < k1) e_loads<DIM, PML>(g, f, cs, o + pl, k + 1, dym, dxm, hx, hy, jdirty, nxt);
+            if (k + 1 < k1)
+                e_loads<DIM, PML, EPS>(g, f, cs, o + pl, k + 1, dym, dxm, hx, hy, jdirty, nxt);
             if (clearJ) {
                 __stcg(f.J[0] + o, 0.f);
                 __stcg(f.J[1] + o, 0.f);
@@ -351,9 +356,15 @@ __global__ void __launch_bounds__(BX * BY) field_e_kernel(GridP g, FieldP f) {
                     tEyz = cpml_pre(f.psi_out[2][1], cur.qz, cur.pz[1], bez, aez, tEyz);
                 }
             }
-            f.En[0][o] = cur.e0 + c2dt * (tExy - tExz) - dte * jx;
-            f.En[1][o] = cur.e1 + c2dt * (tEyz - tEyx) - dte * jy;
-            f.En[2][o] = cur.e2 + c2dt * (tEzx - tEzy) - dte * jz;
+            if (EPS) {  // eps dE/dt = curl H - J (Eq. consteps)
+                f.En[0][o] = cur.e0 + cur.ie * (c2dt * (tExy - tExz) - dte * jx);
+                f.En[1][o] = cur.e1 + cur.ie * (c2dt * (tEyz - tEyx) - dte * jy);
+                f.En[2][o] = cur.e2 + cur.ie * (c2dt * (tEzx - tEzy) - dte * jz);
+            } else {
+                f.En[0][o] = cur.e0 + c2dt * (tExy - tExz) - dte * jx;
+                f.En[1][o] = cur.e1 + c2dt * (tEyz - tEyx) - dte * jy;
+                f.En[2][o] = cur.e2 + c2dt * (tEzx - tEzy) - dte * jz;
+            }
             bxm = cur.bx;
             bym = cur.by;
             cur = nxt;
@@ -386,11 +397,21 @@ cudaError_t launch_field_e(const GridP &g, const FieldP &f, cudaStream_t s) {
               g.dims == 3 ? (g.n[2] + f.zchunk - 1) / f.zchunk : 1);
     const bool pml = f.pml[0] || f.pml[1] || f.pml[2];
     if (g.dims == 3) {
-        field_e_kernel<3, false><<<grid, BX * BY, 0, s>>>(g, f);
-        if (pml) field_e_kernel<3, true><<<grid, BX * BY, 0, s>>>(g, f);
+        if (f.inv_eps) {
+            field_e_kernel<3, false, true><<<grid, BX * BY, 0, s>>>(g, f);
+            if (pml) field_e_kernel<3, true, true><<<grid, BX * BY, 0, s>>>(g, f);
+        } else {
+            field_e_kernel<3, false, false><<<grid, BX * BY, 0, s>>>(g, f);
+            if (pml) field_e_kernel<3, true, false><<<grid, BX * BY, 0, s>>>(g, f);
+        }
     } else {
-        field_e_kernel<2, false><<<grid, BX * BY, 0, s>>>(g, f);
-        if (pml) field_e_kernel<2, true><<<grid, BX * BY, 0, s>>>(g, f);
+        if (f.inv_eps) {
+            field_e_kernel<2, false, true><<<grid, BX * BY, 0, s>>>(g, f);
+            if (pml) field_e_kernel<2, true, true><<<grid, BX * BY, 0, s>>>(g, f);
+        } else {
+            field_e_kernel<2, false, false><<<grid, BX * BY, 0, s>>>(g, f);
+            if (pml) field_e_kernel<2, true, false><<<grid, BX * BY, 0, s>>>(g, f);
+        }
     }
     return cudaGetLastError();
 }

@@ -289,6 +289,7 @@ FieldP field_params(pic_sim *s) {
     f.nbz = s->nbz;
     // the split B pass feeds its interior blocks by TMA where the maps exist
     f.tma_b = (s->tun.field_mode == 2 && s->use_tma && !s->tun.field_plain && s->g.dims == 3) ? 1 : 0;
+    f.inv_eps = s->inv_eps;
     return f;
 }
 
@@ -515,7 +516,33 @@ pic_status pic_set_tuning(pic_sim *s, const pic_tuning *t) {
     if (!s || !t) return fail(s, PIC_EINVAL, "null argument");
     if (s->steps > 0) return fail(s, PIC_ESTATE, "tuning must precede the first step");
     if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (s->inv_eps && (t->field_mode == 1 || t->field_mode == 3))
+        return fail(s, PIC_EINVAL, "a permittivity needs field_mode 2 (the split passes)");
     return pic::apply_tuning(s, t);
+}
+
+pic_status pic_set_permittivity(pic_sim *s, const float *eps_r, size_t n) {
+    if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (!eps_r) {  // back to vacuum
+        dfree(s, s->inv_eps);
+        s->inv_eps = nullptr;
+        return PIC_OK;
+    }
+    if ((long long)n != s->g.ncell)
+        return fail(s, PIC_EINVAL, "permittivity size must equal the cell count");
+    if (s->tun.field_mode != 2)
+        return fail(s, PIC_ESTATE, "a permittivity needs field_mode 2 (the split passes)");
+    std::vector<float> inv(n);
+    for (size_t c = 0; c < n; ++c) {
+        if (!(eps_r[c] >= 1e-6f && eps_r[c] <= 1e6f))  // also rejects NaN
+            return fail(s, PIC_EINVAL, "eps_r must be finite and positive (1e-6 .. 1e6)");
+        inv[c] = 1.0f / eps_r[c];
+    }
+    if (!s->inv_eps && !(s->inv_eps = (float *)dalloc(s, n * sizeof(float))))
+        return fail(s, PIC_ENOMEM, "permittivity");
+    CK(s, cudaMemcpy(s->inv_eps, inv.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    return PIC_OK;
 }
 
 }  // extern "C"
@@ -968,7 +995,7 @@ pic_status pic_diagnostics(pic_sim *s, pic_diag *out) {
         CK(s, launch_rho_deposit(g, species_params(s, sp, sp.cur), sp.desc.q * sp.weight / V,
                                  s->rho, s->stream));
     }
-    CK(s, launch_gauss(g, E, s->rho, s->rho_bg, s->diag_acc, s->stream));
+    CK(s, launch_gauss(g, E, s->inv_eps, s->rho, s->rho_bg, s->diag_acc, s->stream));
     DiagAcc acc;
     CK(s, cudaStreamSynchronize(s->stream));
     CK(s, cudaMemcpy(&acc, s->diag_acc, sizeof(acc), cudaMemcpyDeviceToHost));

@@ -314,6 +314,8 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (!g || !s) return gfail(g, PIC_EINVAL, "null argument");
     if (s->group) return gfail(g, PIC_ESTATE, "simulation already belongs to a group");
     if (nsteps < 0) return gfail(g, PIC_EINVAL, "nsteps must be >= 0");
+    if (s->inv_eps)
+        return gfail(g, PIC_EINVAL, "a simulation with a permittivity steps alone (pic_step)");
     if (g->dims == 0) {
         g->dims = s->g.dims;
         for (int a = 0; a < 3; ++a) g->tile[a] = s->tp.T[a];

@@ -94,6 +94,7 @@ struct FieldP {
     int zchunk;
     int nbx, nby, nbz;   // field-block grid (for jdirty)
     int tma_b;           // 1: the TMA-fed B pass takes the blocks field_b_tma_block admits
+    const float *inv_eps;  // 1 / eps_r per cell (Eq. consteps), or null: vacuum
 };
 
 constexpr int kFieldBX = 32, kFieldBY = 8;
@@ -245,8 +246,8 @@ cudaError_t launch_field_energy(const GridP &g, const float *const *E, const flo
                                 DiagAcc *acc, cudaStream_t s);
 cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V,
                                double *rho, cudaStream_t s);
-cudaError_t launch_gauss(const GridP &g, const float *const *E, const double *rho,
-                         const double *rho_bg, DiagAcc *acc, cudaStream_t s);
+cudaError_t launch_gauss(const GridP &g, const float *const *E, const float *inv_eps,
+                         const double *rho, const double *rho_bg, DiagAcc *acc, cudaStream_t s);
 cudaError_t launch_add_uniform(double *rho, long long n, double v, cudaStream_t s);
 
 // readback helpers (k_diag.cu)

@@ -58,6 +58,7 @@ struct pic_sim {
     float *psi[2][3][4] = {};
     float *cb_e[3] = {}, *ca_e[3] = {}, *cb_h[3] = {}, *ca_h[3] = {};
     uint8_t *mask_d = nullptr;
+    float *inv_eps = nullptr;  // 1 / eps_r per cell, null: vacuum
     std::vector<uint8_t> mask_h;
     uint8_t *jdirty = nullptr;
     int nbx = 1, nby = 1, nbz = 1;

@@ -91,6 +91,7 @@ SIGNATURES = {
     "pic_create": (C.c_int, [C.POINTER(pic_grid_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
     "pic_destroy": (C.c_int, [_H]),
     "pic_set_material_mask": (C.c_int, [_H, C.POINTER(C.c_uint8), C.c_size_t]),
+    "pic_set_permittivity": (C.c_int, [_H, C.POINTER(C.c_float), C.c_size_t]),
     "pic_load_species": (C.c_int, [_H, C.POINTER(pic_species_desc), C.POINTER(pic_particles),
                                    C.POINTER(C.c_int)]),
     "pic_set_tuning": (C.c_int, [_H, C.POINTER(pic_tuning)]),
@@ -216,6 +217,15 @@ def pic_destroy(h):
 def pic_set_material_mask(h, mask):
     m = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
     _check(load_library().pic_set_material_mask(h, _ptr(m, C.c_uint8), m.size), h)
+
+
+def pic_set_permittivity(h, eps_r):
+    """Relative permittivity per cell, [nz][ny][nx] (None: vacuum)."""
+    if eps_r is None:
+        _check(load_library().pic_set_permittivity(h, None, 0), h)
+        return
+    e = np.ascontiguousarray(eps_r, dtype=np.float32).ravel()
+    _check(load_library().pic_set_permittivity(h, _ptr(e, C.c_float), e.size), h)
 
 
 def species_desc(kind, q, m, weight=0.0, omega0=(0, 0, 0), gamma=(0, 0, 0), v_F=0.0,

@@ -612,3 +612,106 @@ def test_tma_passes_with_current_3d_periodic(overlap):
         pic.pic_destroy(h)
         pic.pic_destroy(hp)
         s.close()
+
+
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_permittivity_matches_oracle(overlap):
+    """Eq. consteps with a per-cell eps_r: the metal sphere (free and bound
+    electrons, CPML, plane-wave source) with a dielectric slab (eps_r = 2.5)
+    through it and a second one (eps_r = 6) in vacuum.  Fields match the
+    oracle after 1 step (1e-5) and 40 steps (1e-3); the Gauss residual on D
+    stays at roundoff (FP32 on the GPU, FP64 in the oracle)."""
+    rng = np.random.default_rng(41)
+    # no initial bound displacement: ions at the anchors neutralise the start,
+    # so the Gauss residual on D begins (and must stay) at roundoff
+    grid, mask, species = _sphere_case(rng, n=(32, 28, 24), bc=(0, 0, 0), dscale=0.0)
+    grid["src"] = None
+    n = grid["n"]
+    eps = np.ones((n[2], n[1], n[0]), np.float32)
+    eps[:, :, 12:18] = 2.5
+    eps[:, 2:6, 24:29] = 6.0
+    pic = _pic()
+    s = PR.oracle_sim(grid, mask, species)
+    s.set_permittivity(eps.astype(np.float64))
+    h = PR.gpu_sim(grid, mask, species, tuning=dict(no_overlap=1 - overlap, field_mode=2))
+    pic.pic_set_permittivity(h, eps)
+    try:
+        for nsteps, tol in ((1, 1e-5), (39, 1e-3)):
+            pic.pic_step(h, nsteps)
+            s.step(nsteps)
+            got = PR.gpu_fields(h, grid)
+            for c in range(6):
+                ref = s.field(c)
+                if np.linalg.norm(ref) > 0:
+                    assert PR.rel_l2(got[c], ref) < tol, (c, nsteps, PR.rel_l2(got[c], ref))
+        dg = pic.pic_diagnostics(h)
+        od = s.diag()
+        qs = I.QE * 5.9e28 / 8 / I.EPS0  # one macro-particle's charge density / eps0
+        assert od["gauss_max"] < 1e-10 * qs
+        assert dg["gauss_max"] < 1e-5 * qs
+        assert abs(dg["field_E"] / od["field_E"] - 1) < 1e-3
+    finally:
+        pic.pic_destroy(h)
+        s.close()
+
+
+def test_dielectric_half_space_fresnel_on_gpu():
+    """The Fresnel pin of the oracle run by the GPU path: a pulse in vacuum on
+    an eps_r = 4 half-space reflects 1/3 and transmits 2/3 of its amplitude
+    within 2 %."""
+    nx = 1200
+    n = (nx, 2, 1)
+    d = (1e-9, 1e-9, 1e-9)
+    dt = 0.5 * 1e-9 / (I.C_LIGHT * math.sqrt(2))
+    tau = 0.25e-15
+    grid = dict(dims=2, n=n, d=d, dt=dt, bc=(1, 0, 0), pml_cells=16,
+                src=dict(inc_axis=0, pol_axis=1, src_index=40, E0=1e8,
+                         omega=2 * math.pi * I.C_LIGHT / 80e-9, tau=tau, t0=3 * tau))
+    eps = np.ones((1, 2, nx), np.float32)
+    eps[..., 700:] = 4.0
+    pic = _pic()
+    h = PR.gpu_sim(grid, None, [])
+    pic.pic_set_permittivity(h, eps)
+    pa, pb = 200, 800
+    nsteps = int((3 * tau * I.C_LIGHT / 1e-9 + 1560) / (I.C_LIGHT * dt / 1e-9))
+    t, ea, eb = [], [], []
+    try:
+        for it in range(nsteps):
+            pic.pic_step(h, 1)
+            E = pic.pic_read_fields(h, pic.PIC_EY, I.grid_shape(n))[0, 0, 0]
+            t.append((it + 1) * dt)
+            ea.append(abs(E[pa]))
+            eb.append(abs(E[pb]))
+    finally:
+        pic.pic_destroy(h)
+    t, ea, eb = np.array(t), np.array(ea), np.array(eb)
+    split = 3 * tau + (pa - 40 + 500) * 1e-9 / I.C_LIGHT
+    inc, ref, tra = ea[t < split].max(), ea[t > split].max(), eb.max()
+    assert abs(ref / inc - 1 / 3) < 0.02 / 3
+    assert abs(tra / inc - 2 / 3) < 0.02 * 2 / 3
+
+
+def test_permittivity_arguments():
+    """Wrong size, non-positive or NaN values and the fused field modes are
+    refused with PIC_EINVAL / PIC_ESTATE; NULL returns to vacuum."""
+    pic = _pic()
+    n = (8, 8, 8)
+    grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
+    h = PR.gpu_sim(grid, None, [])
+    try:
+        good = np.full((8, 8, 8), 2.0, np.float32)
+        for bad in (np.full(10, 2.0, np.float32), -good, good * np.nan, good * 0):
+            with pytest.raises(pic.PicError) as e:
+                pic.pic_set_permittivity(h, bad)
+            assert e.value.status == pic.PIC_EINVAL
+        pic.pic_set_permittivity(h, good)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_set_tuning(h, field_mode=3)
+        assert e.value.status == pic.PIC_EINVAL
+        pic.pic_set_permittivity(h, None)
+        pic.pic_set_tuning(h, field_mode=1)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_set_permittivity(h, good)
+        assert e.value.status == pic.PIC_ESTATE
+    finally:
+        pic.pic_destroy(h)
