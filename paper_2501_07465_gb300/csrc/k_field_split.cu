@@ -216,9 +216,9 @@ struct ELoads {
 };
 
 template <int DIM, bool PML, bool EPS>
-__device__ inline void e_loads(const GridP &g, const FieldP &f, const ColSlab &cs, long long o,
-                               int k, long long dym, int dxm, bool hx, bool hy, bool jdirty,
-                               ELoads &L) {
+__device__ inline void e_loads(const GridP &g, const FieldP &f, const float *inv_eps,
+                               const ColSlab &cs, long long o, int k, long long dym, int dxm,
+                               bool hx, bool hy, bool jdirty, ELoads &L) {
     L.bx = __ldg(f.Bn[0] + o);
     L.by = __ldg(f.Bn[1] + o);
     L.bz = __ldg(f.Bn[2] + o);
@@ -229,7 +229,7 @@ __device__ inline void e_loads(const GridP &g, const FieldP &f, const ColSlab &c
     L.e0 = __ldg(f.E[0] + o);
     L.e1 = __ldg(f.E[1] + o);
     L.e2 = __ldg(f.E[2] + o);
-    L.ie = EPS ? __ldg(f.inv_eps + o) : 1.f;
+    L.ie = EPS ? __ldg(inv_eps + o) : 1.f;
     L.jx = L.jy = L.jz = 0.f;
     if (jdirty) {  // J is cleared by this thread one plane later
         L.jx = __ldcg(f.J[0] + o);
@@ -267,7 +267,8 @@ __device__ inline float source_value(const FieldP &f) {
 // EPS: a permittivity is set (its own instantiation: the vacuum kernel keeps
 // its registers)
 template <int DIM, bool PML, bool EPS>
-__global__ void __launch_bounds__(BX * BY) field_e_kernel(GridP g, FieldP f) {
+__global__ void __launch_bounds__(BX * BY)
+    field_e_kernel(GridP g, FieldP f, const float *inv_eps) {
     if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
     __shared__ float s_src;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -317,10 +318,11 @@ __global__ void __launch_bounds__(BX * BY) field_e_kernel(GridP g, FieldP f) {
             bym = __ldg(f.Bn[1] + om);
         }
         ELoads cur, nxt;
-        e_loads<DIM, PML, EPS>(g, f, cs, o, k0, dym, dxm, hx, hy, jdirty, cur);
+        e_loads<DIM, PML, EPS>(g, f, inv_eps, cs, o, k0, dym, dxm, hx, hy, jdirty, cur);
         for (int k = k0; k < k1; ++k, o += pl) {
             if (k + 1 < k1)
-                e_loads<DIM, PML, EPS>(g, f, cs, o + pl, k + 1, dym, dxm, hx, hy, jdirty, nxt);
+                e_loads<DIM, PML, EPS>(g, f, inv_eps, cs, o + pl, k + 1, dym, dxm, hx, hy, jdirty,
+                                       nxt);
             if (clearJ) {
                 __stcg(f.J[0] + o, 0.f);
                 __stcg(f.J[1] + o, 0.f);
@@ -392,25 +394,25 @@ cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_e(const GridP &g, const FieldP &f, cudaStream_t s) {
+cudaError_t launch_field_e(const GridP &g, const FieldP &f, const float *inv_eps, cudaStream_t s) {
     dim3 grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY,
               g.dims == 3 ? (g.n[2] + f.zchunk - 1) / f.zchunk : 1);
     const bool pml = f.pml[0] || f.pml[1] || f.pml[2];
     if (g.dims == 3) {
-        if (f.inv_eps) {
-            field_e_kernel<3, false, true><<<grid, BX * BY, 0, s>>>(g, f);
-            if (pml) field_e_kernel<3, true, true><<<grid, BX * BY, 0, s>>>(g, f);
+        if (inv_eps) {
+            field_e_kernel<3, false, true><<<grid, BX * BY, 0, s>>>(g, f, inv_eps);
+            if (pml) field_e_kernel<3, true, true><<<grid, BX * BY, 0, s>>>(g, f, inv_eps);
         } else {
-            field_e_kernel<3, false, false><<<grid, BX * BY, 0, s>>>(g, f);
-            if (pml) field_e_kernel<3, true, false><<<grid, BX * BY, 0, s>>>(g, f);
+            field_e_kernel<3, false, false><<<grid, BX * BY, 0, s>>>(g, f, nullptr);
+            if (pml) field_e_kernel<3, true, false><<<grid, BX * BY, 0, s>>>(g, f, nullptr);
         }
     } else {
-        if (f.inv_eps) {
-            field_e_kernel<2, false, true><<<grid, BX * BY, 0, s>>>(g, f);
-            if (pml) field_e_kernel<2, true, true><<<grid, BX * BY, 0, s>>>(g, f);
+        if (inv_eps) {
+            field_e_kernel<2, false, true><<<grid, BX * BY, 0, s>>>(g, f, inv_eps);
+            if (pml) field_e_kernel<2, true, true><<<grid, BX * BY, 0, s>>>(g, f, inv_eps);
         } else {
-            field_e_kernel<2, false, false><<<grid, BX * BY, 0, s>>>(g, f);
-            if (pml) field_e_kernel<2, true, false><<<grid, BX * BY, 0, s>>>(g, f);
+            field_e_kernel<2, false, false><<<grid, BX * BY, 0, s>>>(g, f, nullptr);
+            if (pml) field_e_kernel<2, true, false><<<grid, BX * BY, 0, s>>>(g, f, nullptr);
         }
     }
     return cudaGetLastError();

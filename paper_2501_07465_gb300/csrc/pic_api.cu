@@ -289,7 +289,6 @@ FieldP field_params(pic_sim *s) {
     f.nbz = s->nbz;
     // the split B pass feeds its interior blocks by TMA where the maps exist
     f.tma_b = (s->tun.field_mode == 2 && s->use_tma && !s->tun.field_plain && s->g.dims == 3) ? 1 : 0;
-    f.inv_eps = s->inv_eps;
     return f;
 }
 
@@ -833,7 +832,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
                 record(s, 3, false);
             }
             record(s, 1, true);
-            CK(s, launch_field_e(s->g, f, s->stream));
+            CK(s, launch_field_e(s->g, f, s->inv_eps, s->stream));
             record(s, 1, false);
             // each pass is one launch, or two (lean and CPML blocks) with CPML,
             // plus the TMA-fed B pass

@@ -94,7 +94,6 @@ struct FieldP {
     int zchunk;
     int nbx, nby, nbz;   // field-block grid (for jdirty)
     int tma_b;           // 1: the TMA-fed B pass takes the blocks field_b_tma_block admits
-    const float *inv_eps;  // 1 / eps_r per cell (Eq. consteps), or null: vacuum
 };
 
 constexpr int kFieldBX = 32, kFieldBY = 8;
@@ -157,7 +156,8 @@ struct TmaMaps {
 // ---------------------------------------------------------------------------
 cudaError_t launch_field(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s);
-cudaError_t launch_field_e(const GridP &g, const FieldP &f, cudaStream_t s);
+// inv_eps: 1 / eps_r per cell (Eq. consteps), or null: vacuum
+cudaError_t launch_field_e(const GridP &g, const FieldP &f, const float *inv_eps, cudaStream_t s);
 cudaError_t launch_field_stream(const GridP &g, const FieldP &f, cudaStream_t s);
 cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s);
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,

@@ -2,6 +2,8 @@
 path (via the C ABI binding) and through the FP64 oracle."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from oracle import oracle as O
@@ -125,3 +127,48 @@ def near_face(X, dims, tol=1e-4):
     """True where a position lies within tol (cells) of a cell face."""
     f = np.asarray(X, np.float64)[:, :dims] % 1.0
     return np.any((f < tol) | (f > 1 - tol), axis=1)
+
+
+# ---------------------------------------------------------------------------
+# the Lorentz half-space reflection case (Sec. 4, Eq. lordielectric)
+# ---------------------------------------------------------------------------
+
+def lorentz_reflection_error(trace, dt, tau, dx, w0, gam, wpb2):
+    """|r(omega)| of the reflected over the incident pulse at the probe (100
+    cells from the source sheet at 40, the half-space from 500) against
+    Fresnel with the bound species' eps(omega) in the exact discrete form of
+    the leapfrog oscillator (Eq. dispersion1 read with sin terms), over the
+    band where the incident spectrum exceeds 20 % of its peak."""
+    t = (np.arange(trace.size) + 1) * dt
+    split = 3 * tau + (60 + 400) * dx / I.C_LIGHT
+    inc = np.fft.rfft(np.where(t < split, trace, 0.0), 1 << 16)
+    ref = np.fft.rfft(np.where(t >= split, trace, 0.0), 1 << 16)
+    w = 2 * np.pi * np.fft.rfftfreq(1 << 16, dt)
+    band = np.abs(inc) > 0.2 * np.abs(inc).max()
+    den = w0 ** 2 * dt ** 2 - 4 * np.sin(w * dt / 2) ** 2 - 1j * gam * dt * np.sin(w * dt)
+    n = np.sqrt((1 + wpb2 * dt ** 2 / den).astype(complex))
+    n = np.where(n.imag < 0, -n, n)
+    r_th = np.abs((1 - n) / (1 + n))
+    r = np.abs(ref) / np.maximum(np.abs(inc), 1e-300)
+    return float(np.abs(r[band] / r_th[band] - 1).max()), w[band]
+
+
+def lorentz_half_space_case():
+    """A 2D3V grid (1600 x 2 cells of 10 nm, CPML along x) with bound
+    electrons (the sphere workload's w0, gamma and N_b, 4 ppc quiet lattice,
+    ions at the anchors) filling x in [500, 1400) cells, and an 800 nm pulse
+    (FWHM 4 fs) launched from x = 40."""
+    nx, dx = 1600, 10e-9
+    dt = 0.5 * dx / (I.C_LIGHT * math.sqrt(2))
+    w0, gam, nb = 2 * np.pi * I.C_LIGHT / 400e-9, 1e14, 0.5 * 5.9e28
+    tau = 4e-15
+    grid = dict(dims=2, n=(nx, 2, 1), d=(dx,) * 3, dt=dt, bc=(1, 0, 0), pml_cells=16,
+                src=dict(inc_axis=0, pol_axis=1, src_index=40, E0=1e7,
+                         omega=2 * np.pi * I.C_LIGHT / 800e-9, tau=tau, t0=3 * tau))
+    mask = np.zeros((1, 2, nx), np.uint8)
+    mask[..., 500:1400] = 1
+    sp = dict(kind=I.BOUND, q=-I.QE, m=I.ME, density=nb, ppc=4, quiet=1, seed=7, E_F=0.0, T=0.0,
+              omega0=(w0,) * 3, gamma=(gam,) * 3, background=1)
+    steps = int((3 * tau + 860 * dx / I.C_LIGHT + 6 * tau + 20e-15) / dt)
+    wpb2 = nb * I.QE ** 2 / (I.EPS0 * I.ME)
+    return grid, mask, sp, steps, dict(dt=dt, tau=tau, dx=dx, w0=w0, gam=gam, wpb2=wpb2)

@@ -715,3 +715,24 @@ def test_permittivity_arguments():
         assert e.value.status == pic.PIC_ESTATE
     finally:
         pic.pic_destroy(h)
+
+
+def test_lorentz_half_space_reflection_spectrum_on_gpu():
+    """The bound species as a dielectric (Sec. 4, Eq. lordielectric): a pulse
+    reflected by a half-space of Lorentz-bound electrons has the spectrum
+    |r(omega)| = |(1 - n)/(1 + n)|, n^2 = 1 + w_pb^2 / (w0^2 - w^2 - i gamma w),
+    within 1 % over w = 0.34 .. 0.66 w0 (|r| about 0.44) -- the closed-form
+    counterpart of the paper's comparison with a full-wave solver."""
+    grid, mask, sp, steps, prm = PR.lorentz_half_space_case()
+    pic = _pic()
+    h = PR.gpu_sim(grid, mask, [sp])
+    trace = np.zeros(steps)
+    try:
+        for it in range(steps):
+            pic.pic_step(h, 1)
+            trace[it] = pic.pic_read_fields(h, pic.PIC_EY, I.grid_shape(grid["n"]))[0, 0, 0, 100]
+    finally:
+        pic.pic_destroy(h)
+    err, band = PR.lorentz_reflection_error(trace, **prm)
+    assert band.min() < 0.36 * prm["w0"] and band.max() > 0.64 * prm["w0"]
+    assert err < 0.01, err

@@ -703,3 +703,35 @@ def test_gauss_law_holds_for_D_in_a_dielectric():
         assert dg["gauss_max"] < 1e-10 * qscale
     assert dg["field_E"] > 0
     s.close()
+
+
+@pytest.mark.slow
+def test_lorentz_half_space_reflection_spectrum():
+    """Sec. 4, Eq. lordielectric: the oracle's bound species, deposit and Yee
+    update together make a medium whose reflection spectrum is Fresnel's with
+    eps(omega) = 1 + w_pb^2 / (w0^2 - w^2 - i gamma w) (discrete form):
+    within 1 % over w = 0.34 .. 0.66 w0 (the setup of the GPU test of the
+    same name)."""
+    from tests import pairs as PR
+    grid, mask, sp, steps, prm = PR.lorentz_half_space_case()
+    g = dict(grid)
+    src = g.pop("src")
+    g.update(src=True, **src)
+    s = O.OracleSim(**g)
+    s.set_mask(mask)
+    n = grid["n"]
+    cell, off, v = O.fd_load(2, n, mask, O.KIND_BOUND, ME, 0.0, 0.0, 0.0, sp["ppc"], True,
+                             sp["seed"], 0)
+    cy, cx = np.divmod(cell, n[0])
+    X = np.stack([cx, cy, np.zeros_like(cx)], 1) + off
+    w = sp["density"] * np.prod(grid["d"]) / sp["ppc"]
+    s.add_species(O.KIND_BOUND, -QE, ME, w, X, v, D=np.zeros_like(X), omega0=sp["omega0"],
+                  gamma=sp["gamma"], bg=1)
+    trace = np.zeros(steps)
+    for it in range(steps):
+        s.step(1)
+        trace[it] = s.field(1)[0, 0, 100]
+    s.close()
+    err, band = PR.lorentz_reflection_error(trace, **prm)
+    assert band.min() < 0.36 * prm["w0"] and band.max() > 0.64 * prm["w0"]
+    assert err < 0.01, err
