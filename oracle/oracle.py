@@ -69,6 +69,9 @@ def _declare(L):
     L.orc_destroy.argtypes = [C.c_void_p]
     L.orc_set_mask.argtypes = [C.c_void_p, _u8p]
     L.orc_set_permittivity.argtypes = [C.c_void_p, _dp]
+    L.orc_set_external_field.argtypes = [C.c_void_p, _dp, _dp, _dp]
+    L.orc_work_function_field.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp]
+    L.orc_set_particle_bc.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64]
     L.orc_add_species.restype = C.c_int
     L.orc_add_species.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                                   _dp, C.c_double, C.c_long, _dp, _dp, _dp, C.c_int]
@@ -252,6 +255,28 @@ class OracleSim:
         assert e.size == np.prod(self.shape)
         self._eps = e
         lib().orc_set_permittivity(self._h, e.ctypes.data_as(_dp))
+
+    def set_external_field(self, E):
+        """External electrostatic field (Ex, Ey, Ez), each [nz][ny][nx] on the
+        E stagger, seen by the particles only (None: remove)."""
+        if E is None:
+            lib().orc_set_external_field(self._h, None, None, None)
+            self._eext = None
+            return
+        arrs = [np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(self.shape))
+                for c in E]
+        self._eext = arrs
+        lib().orc_set_external_field(self._h, *[a.ctypes.data_as(_dp) for a in arrs])
+
+    def work_function_field(self, W_eV):
+        """The work-function barrier field of height W_eV built from the mask
+        (returned, not set)."""
+        out = [np.zeros(self.shape) for _ in range(3)]
+        lib().orc_work_function_field(self._h, float(W_eV), *[a.ctypes.data_as(_dp) for a in out])
+        return out
+
+    def set_particle_bc(self, open_edges=False, p_diffuse=0.0, seed=0):
+        lib().orc_set_particle_bc(self._h, int(bool(open_edges)), float(p_diffuse), int(seed))
 
     def add_species(self, kind, q, m, w, X, V, D=None, omega0=(0, 0, 0), gamma=(0, 0, 0),
                     vF=0.0, bg=0):

@@ -22,7 +22,10 @@
  *      borisrotsol); bound: modified Boris (Eqs. modborisvpm, modborisBrot;
  *      the 3x3 implicit-midpoint system solved by Cramer's rule); Dirac:
  *      Boris with the transverse mass then |v| renormalised to v_F (Sec. 5);
- *      conditional specular reflection at material edges (Sec. 3);
+ *      plus an optional external electrostatic field that only the particles
+ *      see (the work-function barrier of Sec. 3); the particle boundary rule
+ *      of Sec. 3: conditional specular or diffusive reflection at material
+ *      edges, or open edges;
  *      Esirkepov charge-conserving current deposit.
  *   3. Soft plane-wave current sheet added to J.
  *   4. Yee: B^{n+1/2} = B^{n-1/2} - dt (curl E^n + CPML psi),
@@ -52,6 +55,10 @@ static double mu0(void) { return 1.0 / (EPS0 * C_LIGHT * C_LIGHT); }
 enum { KIND_FREE = 0, KIND_BOUND = 1, KIND_DIRAC = 2 };
 enum { BC_PERIODIC = 0, BC_PML = 1 };
 #define MAX_SPECIES 8
+/* fourth Philox counter word of the diffuse-reflection draws */
+#define DIFFUSE_STREAM 0x44494655u
+
+void orc_philox(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out);
 
 typedef struct {
     int kind;
@@ -87,6 +94,15 @@ typedef struct {
     double *be[3], *ae[3], *bh[3], *ah[3];
     uint8_t *mask;
     double *eps_r; /* per-cell relative permittivity (NULL: vacuum) */
+    /* external electrostatic field on the E stagger, seen by the particles
+       only (NULL: none) */
+    double *Eext[3];
+    /* particle boundary at material edges: open_edges = 1 lets particles
+       leave the material; otherwise a fraction p_diffuse of the single-face
+       reflections is diffuse (Philox key diff_seed) */
+    int open_edges;
+    double p_diffuse;
+    uint64_t diff_seed;
     double *rho_bg;
     long step;
     int nsp;
@@ -205,6 +221,7 @@ void orc_destroy(void *h) {
         free(s->be[a]); free(s->ae[a]); free(s->bh[a]); free(s->ah[a]);
     }
     for (int k = 0; k < s->nsp; ++k) { free(s->sp[k].X); free(s->sp[k].D); free(s->sp[k].V); }
+    for (int c = 0; c < 3; ++c) free(s->Eext[c]);
     free(s->mask); free(s->eps_r); free(s->rho_bg);
     free(s);
 }
@@ -226,6 +243,73 @@ void orc_set_permittivity(void *h, const double *eps_r) {
     }
     if (!s->eps_r) s->eps_r = (double *)malloc(s->ncell * sizeof(double));
     memcpy(s->eps_r, eps_r, s->ncell * sizeof(double));
+}
+
+/* External electrostatic field (V/m) on the E stagger, added to the gathered
+   E of every particle and never seen by the Maxwell update (the work-function
+   model of Sec. 3).  ex == NULL removes it. */
+void orc_set_external_field(void *h, const double *ex, const double *ey, const double *ez) {
+    orc_sim *s = (orc_sim *)h;
+    const double *in[3] = {ex, ey, ez};
+    for (int c = 0; c < 3; ++c) {
+        free(s->Eext[c]);
+        s->Eext[c] = NULL;
+    }
+    if (!ex) return;
+    for (int c = 0; c < 3; ++c) {
+        s->Eext[c] = (double *)malloc(s->ncell * sizeof(double));
+        memcpy(s->Eext[c], in[c], s->ncell * sizeof(double));
+    }
+}
+
+/* Vacuum fraction of the cells that share grid node (i, j, k): cells
+   i-1..i, j-1..j, k-1..k (the four cells of the plane in 2D); cells beyond a
+   non-periodic face do not count.  No mask: all material. */
+static double node_vacuum(const orc_sim *s, int i, int j, int k) {
+    int nin = 0, nvac = 0;
+    int kn = s->dims == 3 ? 2 : 1;
+    for (int dk = 0; dk < kn; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                int c[3] = {i - 1 + di, j - 1 + dj, s->dims == 3 ? k - 1 + dk : 0};
+                if (!wrap_index(s, c)) continue;
+                ++nin;
+                if (s->mask && !s->mask[idx3(s, c[0], c[1], c[2])]) ++nvac;
+            }
+    return nin ? (double)nvac / nin : 0.0;
+}
+
+/* Work-function barrier (Sec. 3): the electrostatic potential on the grid
+   nodes is phi = -(W / e) f, f the node's vacuum fraction, so an electron
+   (charge -e) gains potential energy W on leaving the material.  The field
+   E = -grad phi is taken on the Yee stagger: E_a of cell (i, j, k) is
+   -(phi(node + e_a) - phi(node)) / d_a, node = (i, j, k); E_z = 0 in 2D.
+   W in eV; writes ex, ey, ez (ncell each). */
+void orc_work_function_field(void *h, double W_eV, double *ex, double *ey, double *ez) {
+    orc_sim *s = (orc_sim *)h;
+    double *out[3] = {ex, ey, ez};
+    for (int k = 0; k < s->n[2]; ++k)
+        for (int j = 0; j < s->n[1]; ++j)
+            for (int i = 0; i < s->n[0]; ++i) {
+                long c = idx3(s, i, j, k);
+                double phi0 = -W_eV * node_vacuum(s, i, j, k);
+                for (int a = 0; a < 3; ++a) {
+                    if (a == 2 && s->dims == 2) { out[a][c] = 0.0; continue; }
+                    int nb[3] = {i + (a == 0), j + (a == 1), k + (a == 2)};
+                    double phi1 = -W_eV * node_vacuum(s, nb[0], nb[1], nb[2]);
+                    out[a][c] = -(phi1 - phi0) / s->d[a];
+                }
+            }
+}
+
+/* Particle boundary rule at material edges (Sec. 3): open = 1 lets the
+   particles cross; otherwise a reflection across a single face is diffuse
+   with probability p_diffuse (Philox key = seed), specular otherwise. */
+void orc_set_particle_bc(void *h, int open, double p_diffuse, uint64_t seed) {
+    orc_sim *s = (orc_sim *)h;
+    s->open_edges = open;
+    s->p_diffuse = p_diffuse;
+    s->diff_seed = seed;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -434,6 +518,7 @@ static double interp(const orc_sim *s, const double *F, const double *stag, cons
 static void gather(const orc_sim *s, const double *X, double *E, double *B) {
     for (int c = 0; c < 3; ++c) {
         E[c] = interp(s, s->E[c], STAG_E[c], X);
+        if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_E[c], X);
         B[c] = interp(s, s->Bn[c], STAG_B[c], X);
     }
 }
@@ -534,30 +619,70 @@ void orc_deposit_one(void *h, const double *X0, const double *X1, double qw, dou
 /* material-edge reflection (Sec. 3, fully specular scattering)              */
 /* ------------------------------------------------------------------------ */
 
-/* A particle that leaves a material cell for a vacuum cell, or that leaves
-   the domain across a non-periodic face, is reflected specularly at the cell
-   faces it crossed: for every axis a whose cell index changed, the position is
-   mirrored about the crossed face and v_a changes sign.  Returns 1 if the
-   particle was reflected. */
-static int reflect(const orc_sim *s, const double *X0, double *X1, double *v) {
-    int c0[3], c1[3], moved = 0;
+/* Uniform in [0, 1) from the top 24 bits of a Philox word: exact in FP32, so
+   a comparison with an FP32 probability decides alike in any precision. */
+static double u24(uint32_t x) { return (double)(x >> 8) / 16777216.0; }
+
+/* Particle boundary rule (Sec. 3).  A particle that leaves the domain across
+   a non-periodic face is reflected specularly.  A particle that leaves a
+   material cell for a vacuum cell is reflected there too, unless the edges
+   are open.  Reflection: for every axis a whose cell index changed, the
+   position is mirrored about the crossed face; specular reflection also
+   changes the sign of v_a.  A material-edge reflection across a single face
+   is diffuse with probability p: the speed is kept and the new direction is
+   drawn from Lambert's cosine law about the inward normal n -- cos(theta) =
+   sqrt(u1), azimuth 2 pi u2 for 3D velocities; for the in-plane Dirac
+   carriers the 2D law sin(theta) = 2 u1 - 1 in the sheet (v_z stays 0).  The
+   draw of particle p of species k at step n is Philox-4x32-10 with key =
+   seed and counter (p, n, k, DIFFUSE_STREAM): u0 decides (u0 < p, p rounded
+   to FP32), u1 and u2 give the direction.  Returns 1 if reflected. */
+static int reflect(const orc_sim *s, const orc_species *sp, int k, long p, const double *X0,
+                   double *X1, double *v) {
+    int c0[3], c1[3], moved = 0, ncross = 0, axis = 0;
     int na = s->dims;
     for (int a = 0; a < 3; ++a) {
         c0[a] = (int)floor(X0[a]);
         c1[a] = (a < na) ? (int)floor(X1[a]) : c0[a];
-        if (c1[a] != c0[a]) moved = 1;
+        if (c1[a] != c0[a]) { moved = 1; ++ncross; axis = a; }
     }
     if (!moved) return 0;
     int outside = 0;
     for (int a = 0; a < na; ++a)
         if (s->bc[a] != BC_PERIODIC && (c1[a] < 0 || c1[a] >= s->n[a])) outside = 1;
-    int hit = outside || (mask_at(s, c0[0], c0[1], c0[2]) && !mask_at(s, c1[0], c1[1], c1[2]));
-    if (!hit) return 0;
+    int edge = !outside && !s->open_edges &&
+               mask_at(s, c0[0], c0[1], c0[2]) && !mask_at(s, c1[0], c1[1], c1[2]);
+    if (!outside && !edge) return 0;
+    int diffuse = 0;
+    double u1 = 0.0, u2 = 0.0;
+    if (edge && ncross == 1 && s->p_diffuse > 0.0 && !(sp->kind == KIND_DIRAC && axis == 2)) {
+        uint32_t ctr[4] = {(uint32_t)p, (uint32_t)s->step, (uint32_t)k, DIFFUSE_STREAM};
+        uint32_t key[2] = {(uint32_t)s->diff_seed, (uint32_t)(s->diff_seed >> 32)};
+        uint32_t r[4];
+        orc_philox(ctr, key, r);
+        diffuse = u24(r[0]) < (double)(float)s->p_diffuse;
+        u1 = u24(r[1]);
+        u2 = u24(r[2]);
+    }
     for (int a = 0; a < na; ++a) {
         if (c1[a] == c0[a]) continue;
         double face = (double)(c1[a] > c0[a] ? c1[a] : c0[a]);
         X1[a] = 2.0 * face - X1[a];
-        v[a] = -v[a];
+        if (!diffuse) v[a] = -v[a];
+    }
+    if (diffuse) {
+        const double nin = c1[axis] > c0[axis] ? -1.0 : 1.0; /* inward normal along axis */
+        const double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (sp->kind == KIND_DIRAC) {
+            const double st = 2.0 * u1 - 1.0, ct = sqrt(1.0 - st * st);
+            v[axis] = nin * speed * ct;
+            v[1 - axis] = speed * st;
+            v[2] = 0.0;
+        } else {
+            const double ct = sqrt(u1), st = sqrt(1.0 - u1), ph = 2.0 * PI * u2;
+            v[axis] = nin * speed * ct;
+            v[(axis + 1) % 3] = speed * st * cos(ph);
+            v[(axis + 2) % 3] = speed * st * sin(ph);
+        }
     }
     return 1;
 }
@@ -672,7 +797,7 @@ static void yee_update(orc_sim *s) {
 /* one PIC step                                                               */
 /* ------------------------------------------------------------------------ */
 
-static void push_species(orc_sim *s, orc_species *sp) {
+static void push_species(orc_sim *s, orc_species *sp, int k) {
     const double dt = s->dt;
     for (long p = 0; p < sp->n; ++p) {
         double X0[3], X1[3], E[3], B[3];
@@ -687,7 +812,7 @@ static void push_species(orc_sim *s, orc_species *sp) {
             if (sp->kind == KIND_FREE) orc_push_free(v, E, B, sp->q, sp->m, dt);
             else orc_push_dirac(v, E, B, sp->q, sp->m, dt, sp->vF);
             for (int a = 0; a < 3; ++a) X1[a] = X0[a] + (a < s->dims ? dt * v[a] / s->d[a] : 0.0);
-            sp->nrefl += reflect(s, X0, X1, v);
+            sp->nrefl += reflect(s, sp, k, p, X0, X1, v);
         }
         esirkepov(s, X0, X1, sp->q * sp->w, v[2]);
         if (sp->kind != KIND_BOUND) {
@@ -708,7 +833,7 @@ void orc_step(void *h, int nsteps) {
     orc_sim *s = (orc_sim *)h;
     for (int it = 0; it < nsteps; ++it) {
         compute_Bn(s);
-        for (int k = 0; k < s->nsp; ++k) push_species(s, &s->sp[k]);
+        for (int k = 0; k < s->nsp; ++k) push_species(s, &s->sp[k], k);
         source_current(s);
         yee_update(s);
         for (int c = 0; c < 3; ++c) {

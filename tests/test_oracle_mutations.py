@@ -53,6 +53,28 @@ MUTATIONS = [
      "test_gauss_law_holds_for_D_in_a_dielectric"),
     ("permittivity not applied", "double er = s->eps_r ? s->eps_r[c] : 1.0;", "double er = 1.0;",
      "test_dielectric_half_space_fresnel"),
+    ("work-function potential sign", "out[a][c] = -(phi1 - phi0) / s->d[a];",
+     "out[a][c] = (phi1 - phi0) / s->d[a];",
+     "test_work_function_planar_barrier_closed_form or test_potential_wall"),
+    ("node vacuum fraction cell offset", "int c[3] = {i - 1 + di, j - 1 + dj,",
+     "int c[3] = {i + di, j - 1 + dj,", "test_work_function_planar_barrier_closed_form"),
+    ("external field on the B stagger",
+     "if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_E[c], X);",
+     "if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_B[c], X);",
+     "test_external_field_gather_is_exact_for_linear_fields"),
+    ("open edges ignored", "int edge = !outside && !s->open_edges &&", "int edge = !outside &&",
+     "test_open_edges_let_particles_leave"),
+    ("Lambert law without the square root", "const double ct = sqrt(u1), st = sqrt(1.0 - u1)",
+     "const double ct = u1, st = sqrt(1.0 - u1 * u1)",
+     "test_diffuse_reflection_follows_lambert_law_3d"),
+    ("diffuse re-emission outward", "const double nin = c1[axis] > c0[axis] ? -1.0 : 1.0;",
+     "const double nin = c1[axis] > c0[axis] ? 1.0 : -1.0;",
+     "test_diffuse_reflection_follows_lambert_law_3d"),
+    ("diffuse decision word", "diffuse = u24(r[0]) <", "diffuse = u24(r[3]) <",
+     "test_diffuse_fraction_and_draw_layout"),
+    ("2D law uniform in angle", "const double st = 2.0 * u1 - 1.0, ct = sqrt(1.0 - st * st);",
+     "const double st = sin(PI * (u1 - 0.5)), ct = sqrt(1.0 - st * st);",
+     "test_diffuse_reflection_of_dirac_carriers_is_2d_lambert"),
 ]
 
 

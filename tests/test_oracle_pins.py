@@ -735,3 +735,256 @@ def test_lorentz_half_space_reflection_spectrum():
     err, band = PR.lorentz_reflection_error(trace, **prm)
     assert band.min() < 0.36 * prm["w0"] and band.max() > 0.64 * prm["w0"]
     assert err < 0.01, err
+
+
+# ---------------------------------------------------------------------------
+# particle boundary variants (Sec. 3): work-function barrier, open edges,
+# diffusive reflection
+# ---------------------------------------------------------------------------
+
+def _slab_sim(n=(24, 4, 4), lo=6, hi=14, dims=3, d=(0.45e-9, 0.5e-9, 0.4e-9), axis=0):
+    dt = 0.5 * min(d[:dims]) / (C * math.sqrt(dims))
+    s = O.OracleSim(dims=dims, n=n, d=d, dt=dt, bc=(0, 0, 0), pml_cells=0)
+    m = np.zeros(s.shape, np.uint8)
+    sl = [slice(None)] * 3
+    sl[2 - axis] = slice(lo, hi)
+    m[tuple(sl)] = 1
+    s.set_mask(m)
+    return s, m
+
+
+@pytest.mark.parametrize("dims,axis", [(3, 0), (3, 1), (3, 2), (2, 0), (2, 1)])
+def test_work_function_planar_barrier_closed_form(dims, axis):
+    """A planar surface: the node potential steps 0 -> -W/2 -> -W (vacuum
+    fraction 0, 1/2, 1), so E along the normal is W / (2 d) on the two half
+    nodes beside each face (sign: pushing electrons back into the slab) and
+    zero elsewhere; the tangential components vanish."""
+    n = [10, 10, 10 if dims == 3 else 1]
+    s, _ = _slab_sim(n=tuple(n), lo=3, hi=7, dims=dims, axis=axis)
+    d = (0.45e-9, 0.5e-9, 0.4e-9)
+    W = 4.3
+    E = s.work_function_field(W)
+    for c in range(3):
+        if c != axis:
+            assert np.all(E[c] == 0.0)
+    line = np.moveaxis(E[axis], 2 - axis, -1).reshape(-1, n[axis])
+    want = np.zeros(n[axis])
+    # face at 3 (vacuum below): an electron there is pushed up, E < 0
+    want[2] = want[3] = -W / (2 * d[axis])
+    # face at 7 (vacuum above): pushed down, E > 0
+    want[6] = want[7] = W / (2 * d[axis])
+    for row in line:
+        np.testing.assert_allclose(row, want, rtol=1e-14, atol=0)
+
+
+def test_work_function_corner_and_gradient_invariants():
+    """A material cube in vacuum: hand-computed values at an outer corner
+    (node vacuum fraction 7/8) and edge (3/4), and the field is a discrete
+    gradient: its Yee curl vanishes everywhere."""
+    d = (0.45e-9, 0.5e-9, 0.4e-9)
+    s = O.OracleSim(dims=3, n=(9, 8, 7), d=d, dt=1e-19, bc=(0, 1, 0), pml_cells=1)
+    m = np.zeros(s.shape, np.uint8)
+    m[2:5, 2:6, 3:7] = 1          # z in [2,5), y in [2,6), x in [3,7)
+    s.set_mask(m)
+    W = 3.0
+    ex, ey, ez = s.work_function_field(W)
+    # E_x of cell (2, 2, 2) sits between nodes (2,2,2) (vacuum fraction 1,
+    # outside the cube) and (3,2,2) (the cube's corner: 7/8)
+    assert ex[2, 2, 2] == pytest.approx(W * (7 / 8 - 1) / d[0], rel=1e-14)
+    # E_x of cell (3, 3, 2): node (3,3,2) on an edge (3/4) -> (4,3,2) on a face (1/2)
+    assert ex[2, 3, 3] == pytest.approx(W * (1 / 2 - 3 / 4) / d[0], rel=1e-14)
+    # E_z of cell (4, 4, 4): nodes (4,4,4) inside (0) -> (4,4,5) on the top face (1/2)
+    assert ez[4, 4, 4] == pytest.approx(W * (1 / 2 - 0) / d[2], rel=1e-14)
+    # the Yee curl of a gradient is zero (interior cells)
+    scale = W / min(d)
+    cxy = (ey[:, :-1, 1:] - ey[:, :-1, :-1]) / d[0] - (ex[:, 1:, :-1] - ex[:, :-1, :-1]) / d[1]
+    cyz = (ez[:-1, 1:, :] - ez[:-1, :-1, :]) / d[1] - (ey[1:, :-1, :] - ey[:-1, :-1, :]) / d[2]
+    czx = (ex[1:, :, :-1] - ex[:-1, :, :-1]) / d[2] - (ez[:-1, :, 1:] - ez[:-1, :, :-1]) / d[0]
+    for cc in (cxy, cyz, czx):
+        assert np.abs(cc).max() < 1e-12 * scale / min(d)
+
+
+def test_external_field_gather_is_exact_for_linear_fields():
+    """The external field is interpolated on the E stagger like E itself: a
+    field linear in position (sampled at the E nodes) is reproduced exactly
+    while the Maxwell E stays zero."""
+    d = (1e-9, 1.1e-9, 0.9e-9)
+    s = O.OracleSim(dims=3, n=(8, 7, 6), d=d, dt=1e-18, bc=(0, 0, 0), pml_cells=0)
+    kk, jj, ii = np.meshgrid(np.arange(6), np.arange(7), np.arange(8), indexing="ij")
+    coef = [(1.0, -2.0, 0.5, 3.0), (-0.7, 0.3, 1.1, -2.0), (0.2, 0.9, -1.3, 1.0)]
+    stag = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5)]
+    E = []
+    for c in range(3):
+        a, b, e, f = coef[c]
+        E.append(1e6 * (a * (ii + stag[c][0]) + b * (jj + stag[c][1]) + e * (kk + stag[c][2]) + f))
+    s.set_external_field(E)
+    for X in ([2.3, 3.7, 2.1], [4.9, 1.2, 3.5], [3.5, 3.5, 2.5]):
+        Eg, Bg = s.gather(np.array(X))
+        for c in range(3):
+            a, b, e, f = coef[c]
+            assert Eg[c] == pytest.approx(1e6 * (a * X[0] + b * X[1] + e * X[2] + f), rel=1e-12)
+        assert np.all(Bg == 0.0)
+    assert np.all(s.field(0) == 0.0)
+
+
+def _wall_run(K_over_W, W=4.0, vt=(3e4, -2e4)):
+    s, _ = _slab_sim()
+    s.set_external_field(s.work_function_field(W))
+    s.set_particle_bc(open_edges=True)
+    v0 = math.sqrt(2 * K_over_W * W * QE / ME)
+    s.add_species(O.KIND_FREE, -QE, ME, 1e-12, [[10.3, 1.5, 2.2]], [[v0, vt[0], vt[1]]])
+    for _ in range(400):
+        s.step(50)
+        X, V, _, nr = s.species(0)
+        if X[0, 0] > 18.0 or (X[0, 0] < 10.3 and V[0, 0] < 0):
+            return X[0], V[0], nr
+    raise AssertionError("particle neither escaped nor came back")
+
+
+@pytest.mark.parametrize("K_over_W", [0.5, 0.9, 1.1, 2.0])
+def test_potential_wall_reflects_below_W_and_takes_W_above(K_over_W):
+    """An electron meeting the work-function barrier of height W with normal
+    kinetic energy K (open edges, negligible weight): K < W -> it turns back
+    with its normal speed; K > W -> it leaves with normal energy K - W.  The
+    tangential velocity is untouched (the barrier field is along the
+    normal)."""
+    W = 4.0
+    X, V, nr = _wall_run(K_over_W, W)
+    Kx = 0.5 * ME * V[0] ** 2 / (W * QE)
+    if K_over_W < 1:
+        assert V[0] < 0 and X[0] < 14
+        assert Kx == pytest.approx(K_over_W, rel=1e-5)
+    else:
+        assert V[0] > 0 and X[0] > 18
+        assert Kx == pytest.approx(K_over_W - 1.0, rel=1e-4)
+    np.testing.assert_allclose(V[1:], [3e4, -2e4], rtol=1e-8)
+    assert nr == 0
+
+
+def _outgoing(n_part, seed, dims=3, kind=O.KIND_FREE, vF=1e6):
+    """Particles just inside the face x = 14 of the slab, all crossing it in
+    the first step; (X, V) in cell units and m/s."""
+    rng = np.random.default_rng(seed)
+    d0 = 0.45e-9
+    dt = 0.5 * min((0.45e-9, 0.5e-9, 0.4e-9)[:dims]) / (C * math.sqrt(dims))
+    # transverse offsets in [0.25, 0.75): only the x face is crossed
+    yz = rng.integers(0, 4, (n_part, 2)) + 0.25 + 0.5 * rng.random((n_part, 2))
+    if kind == O.KIND_DIRAC:
+        th = rng.uniform(-1.2, 1.2, n_part)
+        V = np.column_stack([vF * np.cos(th), vF * np.sin(th), np.zeros(n_part)])
+    else:
+        V = rng.normal(size=(n_part, 3)) * 2e5
+        V[:, 0] = 0.1 * d0 / dt * (1.0 + rng.random(n_part))
+    # the face is reached 5 % to 95 % into the first step
+    x0 = 14.0 - (0.05 + 0.9 * rng.random(n_part)) * V[:, 0] * dt / d0
+    X = np.column_stack([x0, yz[:, 0], yz[:, 1] if dims == 3 else np.zeros(n_part)])
+    return X, V
+
+
+def test_open_edges_let_particles_leave():
+    """Open edges: a particle that crosses the material surface is not
+    reflected and moves ballistically (E = B = 0, negligible weight); with
+    the default rule the same particles are all reflected."""
+    X0, V0 = _outgoing(200, 3)
+    for open_edges in (True, False):
+        s, _ = _slab_sim()
+        s.set_particle_bc(open_edges=open_edges)
+        s.add_species(O.KIND_FREE, -QE, ME, 1e-12, X0, V0)
+        s.step(1)
+        X, V, _, nr = s.species(0)
+        ballistic = X0 + V0 * s.dt / np.array([0.45e-9, 0.5e-9, 0.4e-9])
+        if open_edges:
+            assert nr == 0
+            np.testing.assert_allclose(X, ballistic, rtol=0, atol=1e-9)
+            np.testing.assert_allclose(V, V0, rtol=1e-9)
+        else:
+            assert nr == len(X0)
+            assert np.all(X[:, 0] < 14.0)
+
+
+def test_diffuse_probability_zero_is_specular():
+    """p = 0 takes no draw: the step is the specular rule bit for bit."""
+    X0, V0 = _outgoing(300, 4)
+    out = []
+    for p in (None, 0.0):
+        s, _ = _slab_sim()
+        if p is not None:
+            s.set_particle_bc(p_diffuse=p, seed=77)
+        s.add_species(O.KIND_FREE, -QE, ME, 1e-12, X0, V0)
+        s.step(3)
+        out.append(s.species(0))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][3] == out[1][3] == len(X0)
+
+
+def _diffuse_once(n_part, p, seed, dims=3, kind=O.KIND_FREE, vF=1e6, key=1234):
+    X0, V0 = _outgoing(n_part, seed, dims, kind, vF)
+    n = (24, 4, 4) if dims == 3 else (24, 4, 1)
+    s, _ = _slab_sim(n=n, dims=dims)
+    s.set_particle_bc(p_diffuse=p, seed=key)
+    if kind == O.KIND_DIRAC:
+        s.add_species(kind, -QE, 0.1 * ME, 1e-12, X0, V0, vF=vF)
+    else:
+        s.add_species(kind, -QE, ME, 1e-12, X0, V0)
+    s.step(1)
+    X, V, _, nr = s.species(0)
+    return s, X0, V0, X, V, nr
+
+
+def test_diffuse_reflection_follows_lambert_law_3d():
+    """p = 1: every reflection re-emits the particle with its speed into the
+    material side with Lambert's cosine law: cos(theta) to the inward normal
+    has density 2 cos(theta) sin(theta), so E[cos] = 2/3 and E[cos^2] = 1/2,
+    and the azimuth about the normal is uniform.  Positions are mirrored about
+    the face as in the specular rule."""
+    N = 20000
+    s, X0, V0, X, V, nr = _diffuse_once(N, 1.0, 5)
+    assert nr == N
+    sp0 = np.linalg.norm(V0, axis=1)
+    np.testing.assert_allclose(np.linalg.norm(V, axis=1), sp0, rtol=1e-12)
+    ct = -V[:, 0] / sp0
+    assert np.all(ct > 0)
+    assert abs(ct.mean() - 2 / 3) < 4 * math.sqrt(1 / 18 / N)
+    assert abs((ct ** 2).mean() - 0.5) < 4 * math.sqrt(1 / 12 / N)
+    ph = np.arctan2(V[:, 2], V[:, 1])
+    for f in (np.cos(ph), np.sin(ph), np.cos(2 * ph)):
+        assert abs(f.mean()) < 4 * math.sqrt(0.5 / N)
+    X1 = X0 + V0 * s.dt / np.array([0.45e-9, 0.5e-9, 0.4e-9])
+    np.testing.assert_allclose(X[:, 0], 28.0 - X1[:, 0], atol=1e-12)
+    np.testing.assert_allclose(X[:, 1:], X1[:, 1:], atol=1e-12)
+
+
+def test_diffuse_reflection_of_dirac_carriers_is_2d_lambert():
+    """Dirac carriers of a 2D sheet: the diffuse direction stays in the sheet
+    (v_z = 0, |v| = v_F) with the 2D cosine law, density cos(theta) / 2 on
+    (-pi/2, pi/2): E[cos] = pi/4, E[cos^2] = 2/3, E[sin] = 0."""
+    N = 20000
+    vF = 1e6
+    s, X0, V0, X, V, nr = _diffuse_once(N, 1.0, 6, dims=2, kind=O.KIND_DIRAC, vF=vF)
+    assert nr == N
+    assert np.all(V[:, 2] == 0.0)
+    np.testing.assert_allclose(np.hypot(V[:, 0], V[:, 1]), vF, rtol=1e-12)
+    ct = -V[:, 0] / vF
+    assert np.all(ct >= 0)
+    var = 2 / 3 - (math.pi / 4) ** 2
+    assert abs(ct.mean() - math.pi / 4) < 4 * math.sqrt(var / N)
+    assert abs((ct ** 2).mean() - 2 / 3) < 4 * math.sqrt(4 / 45 / N)
+    assert abs((V[:, 1] / vF).mean()) < 4 * math.sqrt(1 / 3 / N)
+
+
+def test_diffuse_fraction_and_draw_layout():
+    """p = 0.3: particle j of species 0 at step 0 reflects diffusely exactly
+    when the first word of Philox(key = seed, counter = (j, 0, 0,
+    0x44494655)) gives u = (w >> 8) / 2^24 < p (p in FP32), and the diffuse
+    share is p within the binomial error."""
+    N = 20000
+    p, key = 0.3, 987654321987
+    s, X0, V0, X, V, nr = _diffuse_once(N, p, 7, key=key)
+    spec = np.column_stack([-V0[:, 0], V0[:, 1], V0[:, 2]])
+    diffuse = ~np.all(V == spec, axis=1)
+    want = np.zeros(N, bool)
+    for j in range(N):
+        w = O.philox([j, 0, 0, 0x44494655], [key & 0xFFFFFFFF, key >> 32])
+        want[j] = (int(w[0]) >> 8) / 16777216.0 < float(np.float32(p))
+    assert np.array_equal(diffuse, want)
+    assert abs(diffuse.mean() - p) < 4 * math.sqrt(p * (1 - p) / N)
