@@ -65,8 +65,12 @@ enum { PIC_BG_NONE = 0, PIC_BG_AT_PARTICLES = 1, PIC_BG_UNIFORM = 2 };
 enum {
     PIC_EX = 1 << 0, PIC_EY = 1 << 1, PIC_EZ = 1 << 2,
     PIC_BX = 1 << 3, PIC_BY = 1 << 4, PIC_BZ = 1 << 5,
-    PIC_JX = 1 << 6, PIC_JY = 1 << 7, PIC_JZ = 1 << 8
+    PIC_JX = 1 << 6, PIC_JY = 1 << 7, PIC_JZ = 1 << 8,
+    /* the external field of pic_set_external_field (pic_read_fields only) */
+    PIC_EXTX = 1 << 9, PIC_EXTY = 1 << 10, PIC_EXTZ = 1 << 11
 };
+/* particle boundary rule at material edges (pic_set_particle_bc) */
+enum { PIC_EDGE_REFLECT = 0, PIC_EDGE_OPEN = 1 };
 
 typedef struct pic_sim pic_sim;     /* opaque, owned by the library */
 typedef struct pic_group pic_group; /* opaque batch of simulations */
@@ -166,7 +170,7 @@ typedef struct pic_diag {
     double time;                             /* step * dt, s */
     int nspecies;
     int64_t count[PIC_MAX_SPECIES];          /* particles per species */
-    uint64_t reflections[PIC_MAX_SPECIES];   /* specular reflections so far */
+    uint64_t reflections[PIC_MAX_SPECIES];   /* reflections so far (specular or diffuse) */
     double kinetic[PIC_MAX_SPECIES];         /* sum 1/2 m w |v|^2, J */
     double field_E;                          /* sum eps0 E^2 / 2 dV, J */
     double field_B;                          /* sum B^2 / (2 mu0) dV, J (B on the half step) */
@@ -217,6 +221,52 @@ pic_status pic_set_material_mask(pic_sim *sim, const uint8_t *mask, size_t n);
    refuses it). */
 pic_status pic_set_permittivity(pic_sim *sim, const float *eps_r, size_t n);
 
+/* External electrostatic field (Sec. 3, the work-function model): a static
+   field in V/m on the E stagger of the Yee grid (E_x of cell (i, j, k) at
+   (i+1/2, j, k), E_y at (i, j+1/2, k), E_z at (i, j, k+1/2)) that the
+   particle push adds to the gathered E^n of every species and that the
+   Maxwell update never sees (it enters neither curl E, the E update nor the
+   Gauss diagnostic).  ex, ey, ez: n = number of cells finite doubles each,
+   [nz][ny][nx] (PIC_EINVAL otherwise); the library keeps an FP32 copy, read
+   back with PIC_EXT* in pic_read_fields.  ex == NULL removes the field.
+   Such a simulation steps alone (pic_group_add refuses it). */
+pic_status pic_set_external_field(pic_sim *sim, const double *ex, const double *ey,
+                                  const double *ez, size_t n);
+
+/* The work-function barrier of height W_eV (eV) built on the device from the
+   material mask and set as the external field: node potential
+   phi = -(W / e) f, f the vacuum fraction of the cells that share the node
+   (cells i-1..i, j-1..j, k-1..k; in 2D the four cells of the plane; cells
+   beyond a non-periodic face do not count), and E = -grad phi on the Yee
+   stagger, E_a of cell (i, j, k) = -(phi(node + e_a) - phi(node)) / d_a with
+   node = (i, j, k), E_z = 0 in 2D; an electron gains potential energy W on
+   leaving the material.  Uses the mask set at the time of the call (no mask:
+   all material, the field is removed).  W_eV = 0 removes the field;
+   |W_eV| <= 1e3 and finite (PIC_EINVAL otherwise). */
+pic_status pic_set_work_function(pic_sim *sim, double W_eV);
+
+/* Particle boundary rule at material edges (Sec. 3).
+   PIC_EDGE_REFLECT (default): a free or Dirac particle that moves from a
+   material cell into a vacuum cell is reflected; on every axis whose cell
+   index changed the position is mirrored about the crossed face.  The
+   reflection is specular (those velocity components change sign) or, with
+   probability p_diffuse when a single face was crossed, diffuse: the speed
+   is kept and the direction is drawn from Lambert's cosine law about the
+   inward normal -- cos(theta) = sqrt(u1) and azimuth 2 pi u2 (measured from
+   the next axis in x -> y -> z order) for 3D velocities; for Dirac carriers
+   the in-plane law sin(theta) = 2 u1 - 1 with v_z = 0.  The draws are
+   Philox-4x32-10 with key (seed low word, seed high word) and counter
+   (particle id, step index mod 2^32, species index, 0x44494655);
+   u_i = (word_i >> 8) / 2^24, and the reflection is diffuse when
+   u0 < p_diffuse rounded to FP32.
+   PIC_EDGE_OPEN: particles cross material edges freely (the open surface;
+   with pic_set_work_function, the potential-wall surface); p_diffuse must
+   be 0.
+   Non-periodic domain faces reflect specularly under either rule.  edges
+   outside the enum or p_diffuse outside [0, 1]: PIC_EINVAL.  A simulation
+   with p_diffuse > 0 steps alone (pic_group_add refuses it). */
+pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64_t seed);
+
 /* Add a species (explicit particles or the Fermi-Dirac loader) and sort it
    into tiles.  Re-checks Eq. dtlimit with the plasma and binding frequencies
    of all species so far (PIC_EDTLIMIT).  *species_id receives its index. */
@@ -233,7 +283,8 @@ pic_status pic_step(pic_sim *sim, int nsteps);
 pic_status pic_sync(pic_sim *sim);
 
 /* Copy fields to/from host FP64 arrays (converted from/to the FP32 device
-   fields).  which = OR of PIC_E*, PIC_B*, PIC_J*; the arrays of the selected
+   fields).  which = OR of PIC_E*, PIC_B*, PIC_J* (and, for reading, PIC_EXT*:
+   the external field, PIC_ESTATE if none is set); the arrays of the selected
    components follow one another in bit order, each ncell long; n = total
    doubles.  J is readable only with keep_J.  Synchronous. */
 pic_status pic_read_fields(pic_sim *sim, int which, double *host_out, size_t n);

@@ -1,0 +1,33 @@
+// k_particle_ext.cu -- the particle kernels with the boundary variants of
+// Sec. 3 (external electrostatic field, diffuse reflection), instantiated
+// apart from the plain ones so that the two compile in parallel.
+#include "k_particle.cuh"
+
+namespace pic {
+
+namespace {
+
+template <int DIM>
+cudaError_t ext_setup_dim(size_t smem, int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(particle_kernel<DIM, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM, true>,
+                                                         kThreads, smem);
+}
+
+}  // namespace
+
+cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm) {
+    return dims == 3 ? ext_setup_dim<3>(smem, ctas_per_sm) : ext_setup_dim<2>(smem, ctas_per_sm);
+}
+
+cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,
+                                 cudaStream_t s) {
+    if (nctas < 1) nctas = 1;
+    if (pl.g.dims == 3) particle_kernel<3, true><<<nctas, kThreads, smem, s>>>(pl);
+    else particle_kernel<2, true><<<nctas, kThreads, smem, s>>>(pl);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

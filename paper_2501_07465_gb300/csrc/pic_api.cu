@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -125,12 +126,16 @@ pic_status setup_tiles(pic_sim *s) {
     s->psmem = particle_smem_bytes(tp);
     if (s->psmem > 227 * 1024 - 1024)
         return fail(s, PIC_EINVAL, "particle tile too large for shared memory");
-    int per_sm = 0;
-    CK(s, particle_kernel_setup(dims, s->psmem, &per_sm));
-    if (per_sm < 1) return fail(s, PIC_EINVAL, "particle tile does not fit on an SM");
+    int per_sm = 0, per_sm_ext = 0;
+    CK(s, particle_kernel_setup(dims, s->psmem, &per_sm, &per_sm_ext));
+    if (per_sm < 1 || per_sm_ext < 1)
+        return fail(s, PIC_EINVAL, "particle tile does not fit on an SM");
     // beside the field work, one CTA per SM fewer leaves it room (3 of 4 measured best)
     const int use_sm = (!s->tun.no_overlap && per_sm > 1) ? per_sm - 1 : per_sm;
+    const int use_sm_ext = (!s->tun.no_overlap && per_sm_ext > 1) ? per_sm_ext - 1 : per_sm_ext;
     s->particle_ctas = s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm * s->num_sms;
+    s->particle_ctas_ext =
+        s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm_ext * s->num_sms;
     // tile-indexed buffers
     dfree(s, s->active);
     dfree(s, s->nactive);
@@ -178,6 +183,7 @@ SpeciesP species_params(const pic_sim *s, const Species &sp, int buf) {
     p.jfac[2] = s->g.dims == 3 ? (float)(-qw / (dd[0] * dd[1] * dt))
                                : (float)(qw / (dd[0] * dd[1] * dd[2]));
     p.nrefl = sp.nrefl;
+    p.pid = sp.pid[buf];
     return p;
 }
 
@@ -303,7 +309,12 @@ ParticleLaunch particle_params(pic_sim *s) {
         P.B[a] = s->B[s->fcur][a];
         P.J[a] = s->J[a];
     }
-    P.mask = s->mask_d;
+    P.mask = s->open_edges ? nullptr : s->mask_d;
+    for (int a = 0; a < 3; ++a) P.Eext[a] = s->Eext[a];
+    P.p_diffuse = (float)s->p_diffuse;
+    P.diff_key[0] = (uint32_t)s->diff_seed;
+    P.diff_key[1] = (uint32_t)(s->diff_seed >> 32);
+    P.rng_step = (uint32_t)s->steps;
     P.jdirty = s->jdirty;
     P.nbx = s->nbx;
     P.nby = s->nby;
@@ -315,6 +326,17 @@ ParticleLaunch particle_params(pic_sim *s) {
     P.step_counter = s->step_counter;
     P.status = s->status;
     return P;
+}
+
+bool alloc_external_field(pic_sim *s) {
+    for (int c = 0; c < 3; ++c)
+        if (!s->Eext[c] && !(s->Eext[c] = (float *)dalloc(s, s->g.ncell * sizeof(float))))
+            return false;
+    return true;
+}
+
+int particle_ctas_for(const pic_sim *s, const ParticleLaunch &P) {
+    return particle_launch_ext(P) ? s->particle_ctas_ext : s->particle_ctas;
 }
 
 pic_status check_device_status(pic_sim *s) {
@@ -541,6 +563,62 @@ pic_status pic_set_permittivity(pic_sim *s, const float *eps_r, size_t n) {
     if (!s->inv_eps && !(s->inv_eps = (float *)dalloc(s, n * sizeof(float))))
         return fail(s, PIC_ENOMEM, "permittivity");
     CK(s, cudaMemcpy(s->inv_eps, inv.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    return PIC_OK;
+}
+
+pic_status pic_set_external_field(pic_sim *s, const double *ex, const double *ey,
+                                  const double *ez, size_t n) {
+    if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (!ex) {
+        CK(s, cudaStreamSynchronize(s->stream));
+        for (int c = 0; c < 3; ++c) {
+            dfree(s, s->Eext[c]);
+            s->Eext[c] = nullptr;
+        }
+        return PIC_OK;
+    }
+    if (!ey || !ez) return fail(s, PIC_EINVAL, "ex, ey and ez must all be given");
+    if ((long long)n != s->g.ncell)
+        return fail(s, PIC_EINVAL, "external field size must equal the cell count");
+    const double *in[3] = {ex, ey, ez};
+    std::vector<float> tmp(n);
+    for (int c = 0; c < 3; ++c)
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(in[c][i]) || std::fabs(in[c][i]) > 3e38)
+                return fail(s, PIC_EINVAL, "external field must be finite");
+    if (!alloc_external_field(s)) return fail(s, PIC_ENOMEM, "external field");
+    CK(s, cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < 3; ++c) {
+        for (size_t i = 0; i < n; ++i) tmp[i] = (float)in[c][i];
+        CK(s, cudaMemcpy(s->Eext[c], tmp.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return PIC_OK;
+}
+
+pic_status pic_set_work_function(pic_sim *s, double W_eV) {
+    if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (!(std::fabs(W_eV) <= 1e3)) return fail(s, PIC_EINVAL, "|W| must be finite, <= 1e3 eV");
+    if (W_eV == 0.0 || !s->mask_d) return pic_set_external_field(s, nullptr, nullptr, nullptr, 0);
+    if (!alloc_external_field(s)) return fail(s, PIC_ENOMEM, "external field");
+    CK(s, launch_work_function(s->g, s->mask_d, W_eV, s->Eext, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+pic_status pic_set_particle_bc(pic_sim *s, int edges, double p_diffuse, uint64_t seed) {
+    if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (edges != PIC_EDGE_REFLECT && edges != PIC_EDGE_OPEN)
+        return fail(s, PIC_EINVAL, "edges must be PIC_EDGE_REFLECT or PIC_EDGE_OPEN");
+    if (!(p_diffuse >= 0.0 && p_diffuse <= 1.0))
+        return fail(s, PIC_EINVAL, "p_diffuse must lie in [0, 1]");
+    if (edges == PIC_EDGE_OPEN && p_diffuse != 0.0)
+        return fail(s, PIC_EINVAL, "open edges take no diffuse share");
+    s->open_edges = edges == PIC_EDGE_OPEN;
+    s->p_diffuse = p_diffuse;
+    s->diff_seed = seed;
     return PIC_OK;
 }
 
@@ -813,7 +891,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             if (!s->tun.no_overlap) {
                 CK(s, cudaEventRecord(s->ev_fork, s->stream));
                 record(s, 0, true);
-                CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+                CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
                 record(s, 0, false);
                 CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
                 record(s, 3, true, s->aux);
@@ -824,7 +902,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
                 CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
             } else {
                 record(s, 0, true);
-                CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+                CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
                 record(s, 0, false);
                 record(s, 3, true);
                 CK(s, launch_field_b_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
@@ -845,7 +923,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             f.splitJ = 1;
             CK(s, cudaEventRecord(s->ev_fork, s->stream));
             record(s, 0, true);
-            CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+            CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
             record(s, 0, false);
             CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
             record(s, 1, true, s->aux);
@@ -859,7 +937,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             s->launches += 2 + (stream ? fl : 1);
         } else {
             record(s, 0, true);
-            CK(s, launch_particles(P, s->particle_ctas, s->psmem, s->stream));
+            CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
             record(s, 0, false);
             record(s, 1, true);
             if (stream) CK(s, launch_field_stream(s->g, f, s->stream));
@@ -886,17 +964,22 @@ pic_status pic_read_fields(pic_sim *s, int which, double *out, size_t n) {
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     const long long nc = s->g.ncell;
     int cnt = 0;
-    for (int b = 0; b < 9; ++b) cnt += (which >> b) & 1;
-    if (which <= 0 || which >= (1 << 9) || (long long)n != cnt * nc)
+    for (int b = 0; b < 12; ++b) cnt += (which >> b) & 1;
+    if (which <= 0 || which >= (1 << 12) || (long long)n != cnt * nc)
         return fail(s, PIC_EINVAL, "which/n mismatch");
     if ((which & (PIC_JX | PIC_JY | PIC_JZ)) && !s->tun.keep_J)
         return fail(s, PIC_ESTATE, "J is readable only with keep_J");
+    if ((which & (PIC_EXTX | PIC_EXTY | PIC_EXTZ)) && !s->Eext[0])
+        return fail(s, PIC_ESTATE, "no external field is set");
     CK(s, cudaStreamSynchronize(s->stream));
     std::vector<float> tmp(nc);
     size_t off = 0;
-    for (int b = 0; b < 9; ++b) {
+    for (int b = 0; b < 12; ++b) {
         if (!((which >> b) & 1)) continue;
-        const float *src = b < 3 ? s->E[s->fcur][b] : b < 6 ? s->B[s->fcur][b - 3] : s->J[b - 6];
+        const float *src = b < 3   ? s->E[s->fcur][b]
+                           : b < 6 ? s->B[s->fcur][b - 3]
+                           : b < 9 ? s->J[b - 6]
+                                   : s->Eext[b - 9];
         CK(s, cudaMemcpy(tmp.data(), src, nc * 4, cudaMemcpyDeviceToHost));
         for (long long i = 0; i < nc; ++i) out[off + i] = tmp[i];
         off += nc;

@@ -316,13 +316,16 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (nsteps < 0) return gfail(g, PIC_EINVAL, "nsteps must be >= 0");
     if (s->inv_eps)
         return gfail(g, PIC_EINVAL, "a simulation with a permittivity steps alone (pic_step)");
+    if (s->Eext[0] || s->p_diffuse > 0.0)
+        return gfail(g, PIC_EINVAL,
+                     "a simulation with an external field or diffuse reflection steps alone");
     if (g->dims == 0) {
         g->dims = s->g.dims;
         for (int a = 0; a < 3; ++a) g->tile[a] = s->tp.T[a];
         g->sort_interval = std::max(1, s->tun.sort_interval);
         g->psmem = s->psmem;
         int per_sm = 0;
-        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm));
+        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm, nullptr));
         g->pctas = std::max(1, per_sm) * s->num_sms;
     }
     if (s->g.dims != g->dims) return gfail(g, PIC_EINVAL, "members must share dims");

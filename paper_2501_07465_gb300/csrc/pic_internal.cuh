@@ -30,6 +30,26 @@ __host__ __device__ inline int cell_z(uint32_t c) { return (int)(c >> 22); }
 // Device status word bits (latched, read at sync points).
 enum : int { kStatusBounds = 1, kStatusTimeout = 2 };
 
+// Philox-4x32-10 counter-based generator (Salmon, Moraes, Dror & Shaw, SC'11):
+// ten rounds of the Philox S-box on the counter x with key (k0, k1).
+__device__ inline void philox4x32_10(uint32_t *x, uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, x[0]), lo0 = 0xD2511F53u * x[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, x[2]), lo1 = 0xCD9E8D57u * x[2];
+        uint32_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0;
+        x[1] = lo1;
+        x[2] = y2;
+        x[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Fourth counter word of the diffuse-reflection draws (particle id, step,
+// species, kDiffuseStream).
+constexpr uint32_t kDiffuseStream = 0x44494655u;
+
 struct GridP {
     int dims;
     int n[3];
@@ -60,6 +80,7 @@ struct SpeciesP {
     float dtd[3];                 // dt / d_a
     float jfac[3];                // Esirkepov factors -q w / (d_b d_c dt); 2D J_z: q w / V
     unsigned long long *nrefl;    // device reflection counter
+    const uint32_t *pid;          // particle id (load order), keys the diffuse draws
 };
 
 struct FieldP {
@@ -134,7 +155,12 @@ struct ParticleLaunch {
     const float *E[3];
     const float *B[3];       // B^{n-1/2}
     float *J[3];
-    const uint8_t *mask;     // may be null (all material)
+    const uint8_t *mask;     // may be null (all material, or open material edges)
+    // particle boundary variants (Sec. 3); read by the extended kernel only
+    const float *Eext[3];    // external field on the E stagger, null: none
+    float p_diffuse;         // probability of a diffuse material-edge reflection
+    uint32_t diff_key[2];    // Philox key of the diffuse draws
+    uint32_t rng_step;       // step index of this particle phase (mod 2^32)
     uint8_t *jdirty;
     int nbx, nby, nbz, zchunk;
     const int *active;       // active tile list, largest particle count first
@@ -175,7 +201,18 @@ cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const 
                                   const int *active, const int2 *items, int nitems, int *sched,
                                   int nctas, size_t smem, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
-cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm);
+// ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
+// variants (external field, diffuse reflection)
+cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext);
+// true when the launch needs the kernel with the boundary variants
+inline bool particle_launch_ext(const ParticleLaunch &pl) {
+    return pl.Eext[0] != nullptr || pl.p_diffuse > 0.f;
+}
+
+// boundary variants (k_boundary.cu): the work-function barrier field of
+// height W_eV from the mask (null: all material) into E[3] on the E stagger
+cudaError_t launch_work_function(const GridP &g, const uint8_t *mask, double W_eV,
+                                 float *const E[3], cudaStream_t s);
 
 // sort (k_sort.cu)
 cudaError_t launch_tile_histogram(const GridP &g, const TileP &tp, const uint32_t *cell,

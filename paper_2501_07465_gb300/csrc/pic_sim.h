@@ -59,6 +59,11 @@ struct pic_sim {
     float *cb_e[3] = {}, *ca_e[3] = {}, *cb_h[3] = {}, *ca_h[3] = {};
     uint8_t *mask_d = nullptr;
     float *inv_eps = nullptr;  // 1 / eps_r per cell, null: vacuum
+    // particle boundary variants (Sec. 3)
+    float *Eext[3] = {};       // external field seen by the particles only, null: none
+    int open_edges = 0;        // 1: particles cross material edges
+    double p_diffuse = 0.0;    // share of diffuse material-edge reflections
+    uint64_t diff_seed = 0;    // Philox key of the diffuse draws
     std::vector<uint8_t> mask_h;
     uint8_t *jdirty = nullptr;
     int nbx = 1, nby = 1, nbz = 1;
@@ -73,6 +78,7 @@ struct pic_sim {
     long long rank_cap = 0;
     int **starts_dev = nullptr;
     int particle_ctas = 1;
+    int particle_ctas_ext = 1;  // the same for the kernel with the boundary variants
     size_t psmem = 0;
     int nsp = 0;
     pic::Species sp[kMaxSpecies];

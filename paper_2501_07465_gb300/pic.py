@@ -26,6 +26,8 @@ PIC_FREE, PIC_BOUND, PIC_DIRAC = 0, 1, 2
 PIC_BG_NONE, PIC_BG_AT_PARTICLES, PIC_BG_UNIFORM = 0, 1, 2
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = 1, 2, 4, 8, 16, 32
 PIC_JX, PIC_JY, PIC_JZ = 64, 128, 256
+PIC_EXTX, PIC_EXTY, PIC_EXTZ = 512, 1024, 2048
+PIC_EDGE_REFLECT, PIC_EDGE_OPEN = 0, 1
 PIC_MAX_SPECIES = 8
 
 
@@ -92,6 +94,10 @@ SIGNATURES = {
     "pic_destroy": (C.c_int, [_H]),
     "pic_set_material_mask": (C.c_int, [_H, C.POINTER(C.c_uint8), C.c_size_t]),
     "pic_set_permittivity": (C.c_int, [_H, C.POINTER(C.c_float), C.c_size_t]),
+    "pic_set_external_field": (C.c_int, [_H, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), C.c_size_t]),
+    "pic_set_work_function": (C.c_int, [_H, C.c_double]),
+    "pic_set_particle_bc": (C.c_int, [_H, C.c_int, C.c_double, C.c_uint64]),
     "pic_load_species": (C.c_int, [_H, C.POINTER(pic_species_desc), C.POINTER(pic_particles),
                                    C.POINTER(C.c_int)]),
     "pic_set_tuning": (C.c_int, [_H, C.POINTER(pic_tuning)]),
@@ -226,6 +232,27 @@ def pic_set_permittivity(h, eps_r):
         return
     e = np.ascontiguousarray(eps_r, dtype=np.float32).ravel()
     _check(load_library().pic_set_permittivity(h, _ptr(e, C.c_float), e.size), h)
+
+
+def pic_set_external_field(h, E):
+    """External electrostatic field (Ex, Ey, Ez), each [nz][ny][nx] in V/m on
+    the E stagger, seen by the particles only (None: remove)."""
+    if E is None:
+        _check(load_library().pic_set_external_field(h, None, None, None, 0), h)
+        return
+    arrs = [np.ascontiguousarray(c, dtype=np.float64).ravel() for c in E]
+    _check(load_library().pic_set_external_field(h, *[_ptr(a, C.c_double) for a in arrs],
+                                                 arrs[0].size), h)
+
+
+def pic_set_work_function(h, W_eV):
+    """The work-function barrier of height W_eV built from the mask."""
+    _check(load_library().pic_set_work_function(h, float(W_eV)), h)
+
+
+def pic_set_particle_bc(h, edges=0, p_diffuse=0.0, seed=0):
+    """PIC_EDGE_REFLECT (with a diffuse share p_diffuse) or PIC_EDGE_OPEN."""
+    _check(load_library().pic_set_particle_bc(h, int(edges), float(p_diffuse), int(seed)), h)
 
 
 def species_desc(kind, q, m, weight=0.0, omega0=(0, 0, 0), gamma=(0, 0, 0), v_F=0.0,
