@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--field-mode", type=int, default=2, choices=[1, 2, 3],
                     help="1: fused field update (shared memory), 2: split B / E passes, "
                          "3: one streaming pass")
+    ap.add_argument("--surface", default="specular", choices=["specular", "diffuse", "open", "wall"],
+                    help="particle rule at the metal surface (Sec. 3): specular / diffuse "
+                         "reflection, open edges, or open edges + work-function barrier")
+    ap.add_argument("--diffuse-p", type=float, default=0.5, help="diffuse share, --surface diffuse")
+    ap.add_argument("--work-function", type=float, default=5.1, help="eV, --surface wall")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-graphene", action="store_true", help="skip the graphene-sheet leg")
@@ -228,6 +233,23 @@ def build_sim(pic, I, wl, stream, tuning=None):
     return runner.make_sim(wl, stream, tuning)
 
 
+def apply_surface(pic, h, args):
+    """The particle boundary rule at the material surface (Sec. 3)."""
+    if args.surface == "diffuse":
+        pic.pic_set_particle_bc(h, pic.PIC_EDGE_REFLECT, args.diffuse_p, 20250107)
+    elif args.surface in ("open", "wall"):
+        pic.pic_set_particle_bc(h, pic.PIC_EDGE_OPEN)
+    if args.surface == "wall":
+        pic.pic_set_work_function(h, args.work_function)
+
+
+def surface_config(args):
+    return {"specular": "specular reflection",
+            "diffuse": f"diffuse reflection, p = {args.diffuse_p}",
+            "open": "open edges",
+            "wall": f"open edges + work-function barrier {args.work_function} eV"}[args.surface]
+
+
 def run_gpu(args):
     import torch
 
@@ -259,6 +281,7 @@ def run_gpu(args):
     tuning["field_mode"] = args.field_mode
     split = args.field_mode == 2
     h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning)
+    apply_surface(pic, h, args)
     diag0 = pic.pic_diagnostics(h)
     nparts = sum(diag0["count"])
     nfree, nbound = diag0["count"][0], diag0["count"][1]
@@ -300,7 +323,7 @@ def run_gpu(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     avg = lambda k: tm[f"{k}_ms"] / max(tm[f"{k}_launches"], 1)
     kernels = {"particle": dict(bytes=pb, ms=avg("particle"), total=tm["particle_ms"],
-                                src="k_particle.cu", name="particle_kernel")}
+                                src="k_particle.cuh+k_particle.cu", name="particle_kernel")}
     if split:
         kernels["field_e"] = dict(bytes=fb_e, ms=avg("field"), total=tm["field_ms"],
                                   src="k_field_split.cu", name="field_e_kernel")
@@ -327,7 +350,7 @@ def run_gpu(args):
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        e2e = run_e2e(pic, I, wl, h, stream, nparts)
+        e2e = run_e2e(pic, I, wl, h, stream, nparts, args)
     fp64 = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -353,6 +376,7 @@ def run_gpu(args):
                    "overlap": args.overlap, "particle_ctas": args.particle_ctas or ("3 per SM" if args.overlap else "4 per SM"),
                    "field_mode": {1: "fused (shared memory)", 2: "split B/E passes",
                                   3: "one streaming pass"}[args.field_mode],
+                   "surface": surface_config(args),
                    "l2": "inputs larger than L2 (fields 805 MB, no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": kd["name"], "achieved": achieved,
@@ -503,7 +527,7 @@ def run_serve_leg(args):
             "served": srv, "serial": ser}
 
 
-def run_e2e(pic, I, wl, h_ref, stream, nparts):
+def run_e2e(pic, I, wl, h_ref, stream, nparts, args):
     """Whole job through the public API with host buffers: the particle state
     (pinned host arrays) and the mask go in, the step runs, the diagnostics
     and the fields come back.  Timed on the host clock with the copies
@@ -548,6 +572,7 @@ def run_e2e(pic, I, wl, h_ref, stream, nparts):
                              anchor_off=pdict["anchor_off"].numpy() if "anchor_off" in pdict else None,
                              disp=pdict["disp"].numpy() if "disp" in pdict else None,
                              density=sp["density"])
+    apply_surface(pic, h, args)
     pic.pic_step(h, steps)
     diag = pic.pic_diagnostics(h)
     pic.pic_read_fields(h, 63, (g["n"][2], g["n"][1], g["n"][0]), out=out.numpy())

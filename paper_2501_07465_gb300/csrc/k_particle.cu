@@ -38,10 +38,10 @@ cudaError_t particle_setup_dim(size_t smem, int *ctas_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(batch_particle_kernel<DIM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(particle_kernel<DIM, false>,
+    e = cudaFuncSetAttribute(particle_kernel<DIM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM, false>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM>,
                                                          kThreads, smem);
 }
 
@@ -68,8 +68,8 @@ cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const 
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s) {
     if (nctas < 1) nctas = 1;
     if (particle_launch_ext(pl)) return launch_particles_ext(pl, nctas, smem, s);
-    if (pl.g.dims == 3) particle_kernel<3, false><<<nctas, kThreads, smem, s>>>(pl);
-    else particle_kernel<2, false><<<nctas, kThreads, smem, s>>>(pl);
+    if (pl.g.dims == 3) particle_kernel<3><<<nctas, kThreads, smem, s>>>(pl);
+    else particle_kernel<2><<<nctas, kThreads, smem, s>>>(pl);
     return cudaGetLastError();
 }
 

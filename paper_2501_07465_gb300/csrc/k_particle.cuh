@@ -836,8 +836,9 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
     }
 }
 
+// One particle phase: the persistent CTAs take tiles from the active list.
 template <int DIM, bool X>
-__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
+__device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
     __shared__ int s_next;
@@ -866,6 +867,20 @@ __global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
             P.sched[1] = 0;
         }
     }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
+    particle_phase<DIM, false>(P);
+}
+
+// The kernel with the boundary variants is held to the plain kernel's 64
+// registers (as if 4 CTAs of 256 threads shared an SM): beside the B pass of
+// the overlapped step 3 CTAs per SM run, and the registers they leave free
+// are what lets the B pass co-run.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads, 4) particle_kernel_ext(ParticleLaunch P) {
+    particle_phase<DIM, true>(P);
 }
 
 // Many simulations in one persistent launch: items[i] = (simulation, tile),

@@ -9,10 +9,10 @@ namespace {
 
 template <int DIM>
 cudaError_t ext_setup_dim(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(particle_kernel<DIM, true>,
+    cudaError_t e = cudaFuncSetAttribute(particle_kernel_ext<DIM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM, true>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel_ext<DIM>,
                                                          kThreads, smem);
 }
 
@@ -25,8 +25,8 @@ cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm) {
 cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,
                                  cudaStream_t s) {
     if (nctas < 1) nctas = 1;
-    if (pl.g.dims == 3) particle_kernel<3, true><<<nctas, kThreads, smem, s>>>(pl);
-    else particle_kernel<2, true><<<nctas, kThreads, smem, s>>>(pl);
+    if (pl.g.dims == 3) particle_kernel_ext<3><<<nctas, kThreads, smem, s>>>(pl);
+    else particle_kernel_ext<2><<<nctas, kThreads, smem, s>>>(pl);
     return cudaGetLastError();
 }
 
