@@ -99,8 +99,11 @@ typedef struct pic_grid_desc {
 /* One species.  q, m in C and kg; weight = physical particles per
    macro-particle (ignored by the Fermi-Dirac loader, which sets it to
    density * cell volume / ppc).  omega0 / gamma: binding frequency and
-   damping of PIC_BOUND (Eq. modlorentz; gamma must be isotropic: the three
-   entries equal).  v_F: Fermi velocity of PIC_DIRAC (m is then the averaged
+   damping of PIC_BOUND per axis (Eq. modlorentz with diagonal tensors;
+   gamma finite and >= 0, PIC_EINVAL otherwise; unequal gamma entries take
+   the general 3x3 solve of the modified Boris rotation in the kernel with
+   the boundary variants, and such a simulation steps alone: pic_group_add
+   refuses it).  v_F: Fermi velocity of PIC_DIRAC (m is then the averaged
    transverse mass p_F / (2 v_F) of Sec. 5).  background: PIC_BG_*. */
 typedef struct pic_species_desc {
     int kind;

@@ -293,11 +293,15 @@ __device__ inline void boris(float *v, const float *E, const float *B, float h) 
     v[2] = (s * vm2 + 2.f * (b2 * vb + c2)) * inv + h * E[2];
 }
 
-// Modified Boris for bound species (Appendix A.2, isotropic gamma):
+// Modified Boris for bound species (Appendix A.2):
 // kick = h E - (dt/2) w0^2 D; v- = v + kick; solve
-// (1 + g) v+ - v+ x b = (1 - g) v- + v- x b, g = gamma dt / 2, in closed form
-// v+ = (a^2 w + a (w x b) + (w.b) b) / (a (a^2 + |b|^2)), a = 1 + g,
-// w = (1 - g) v- + v- x b; v = v+ + kick; D += dt v.
+// (1 + G) v+ - v+ x b = (1 - G) v- + v- x b, G = diag(gamma_a dt / 2), i.e.
+// (diag(a) + [b]x) v+ = w with a = 1 + G, w = (1 - G) v- + v- x b;
+// v = v+ + kick; D += dt v.  Isotropic gamma (the plain kernel, and the
+// variant kernel when the entries are equal): the closed form
+// v+ = (a^2 w + a (w x b) + (w.b) b) / (a (a^2 + |b|^2)).  Diagonal gamma
+// (variant kernel only): v+ = adj(M) w / det(M), M = diag(a) + [b]x.
+template <bool X>
 __device__ inline void bound_push(float *v, float *D, const float *E, const float *B,
                                   const SpeciesP &s) {
     const float h = s.hq;
@@ -306,6 +310,26 @@ __device__ inline void bound_push(float *v, float *D, const float *E, const floa
     float k2 = h * E[2] - s.hw0sq[2] * D[2];
     float vm0 = v[0] + k0, vm1 = v[1] + k1, vm2 = v[2] + k2;
     float b0 = h * B[0], b1 = h * B[1], b2 = h * B[2];
+    if (X && s.aniso) {
+        const float a0 = 1.f + s.gdt2v[0], a1 = 1.f + s.gdt2v[1], a2 = 1.f + s.gdt2v[2];
+        const float w0 = (1.f - s.gdt2v[0]) * vm0 + (vm1 * b2 - vm2 * b1);
+        const float w1 = (1.f - s.gdt2v[1]) * vm1 + (vm2 * b0 - vm0 * b2);
+        const float w2 = (1.f - s.gdt2v[2]) * vm2 + (vm0 * b1 - vm1 * b0);
+        const float inv = 1.0f / (a0 * a1 * a2 + a0 * b0 * b0 + a1 * b1 * b1 + a2 * b2 * b2);
+        const float p0 = ((a1 * a2 + b0 * b0) * w0 + (b0 * b1 + a2 * b2) * w1 +
+                          (b0 * b2 - a1 * b1) * w2) * inv;
+        const float p1 = ((b0 * b1 - a2 * b2) * w0 + (a0 * a2 + b1 * b1) * w1 +
+                          (b1 * b2 + a0 * b0) * w2) * inv;
+        const float p2 = ((b0 * b2 + a1 * b1) * w0 + (b1 * b2 - a0 * b0) * w1 +
+                          (a0 * a1 + b2 * b2) * w2) * inv;
+        v[0] = p0 + k0;
+        v[1] = p1 + k1;
+        v[2] = p2 + k2;
+        D[0] += s.dt * v[0];
+        D[1] += s.dt * v[1];
+        D[2] += s.dt * v[2];
+        return;
+    }
     float a = 1.f + s.gdt2, cc = 1.f - s.gdt2;
     float w0 = cc * vm0 + (vm1 * b2 - vm2 * b1);
     float w1 = cc * vm1 + (vm2 * b0 - vm0 * b2);
@@ -609,7 +633,7 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, lo
         int gg[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
         gather<DIM>(glob, gg, f0, E, B);
     }
-    bound_push(v, D, E, B, s);
+    bound_push<X>(v, D, E, B, s);
     float dF[3] = {0.f, 0.f, 0.f};
     int sh[3] = {0, 0, 0};
     bool jump = false;

@@ -175,6 +175,8 @@ SpeciesP species_params(const pic_sim *s, const Species &sp, int buf) {
     p.tile_start = sp.tile_start;
     p.hq = (float)(d.q * dt / (2.0 * d.m));
     p.gdt2 = (float)(0.5 * d.gamma[0] * dt);
+    for (int a = 0; a < 3; ++a) p.gdt2v[a] = (float)(0.5 * d.gamma[a] * dt);
+    p.aniso = d.kind == PIC_BOUND && !(d.gamma[0] == d.gamma[1] && d.gamma[1] == d.gamma[2]);
     p.vF = (float)d.v_F;
     p.dt = (float)dt;
     const double qw = d.q * sp.weight;
@@ -670,8 +672,9 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
     if (d->kind != PIC_FREE && d->kind != PIC_BOUND && d->kind != PIC_DIRAC)
         return fail(s, PIC_EINVAL, "unknown species kind");
     if (!(d->m > 0) || d->q == 0) return fail(s, PIC_EINVAL, "mass must be > 0 and charge != 0");
-    if (d->kind == PIC_BOUND && !(d->gamma[0] == d->gamma[1] && d->gamma[1] == d->gamma[2]))
-        return fail(s, PIC_EINVAL, "bound species need an isotropic gamma");
+    for (int a = 0; a < 3; ++a)
+        if (!(d->gamma[a] >= 0.0 && d->gamma[a] < 1e300))  // also rejects NaN
+            return fail(s, PIC_EINVAL, "gamma must be finite and >= 0");
     if (d->kind == PIC_DIRAC && !(d->v_F > 0)) return fail(s, PIC_EINVAL, "Dirac species need v_F > 0");
     if (d->background < PIC_BG_NONE || d->background > PIC_BG_UNIFORM)
         return fail(s, PIC_EINVAL, "unknown background mode");

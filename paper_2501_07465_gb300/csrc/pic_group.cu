@@ -319,6 +319,11 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (s->Eext[0] || s->p_diffuse > 0.0)
         return gfail(g, PIC_EINVAL,
                      "a simulation with an external field or diffuse reflection steps alone");
+    for (int k = 0; k < s->nsp; ++k) {
+        const double *gm = s->sp[k].desc.gamma;
+        if (s->sp[k].desc.kind == PIC_BOUND && !(gm[0] == gm[1] && gm[1] == gm[2]))
+            return gfail(g, PIC_EINVAL, "a simulation with an anisotropic gamma steps alone");
+    }
     if (g->dims == 0) {
         g->dims = s->g.dims;
         for (int a = 0; a < 3; ++a) g->tile[a] = s->tp.T[a];

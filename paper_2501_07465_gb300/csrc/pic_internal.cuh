@@ -74,7 +74,9 @@ struct SpeciesP {
     const int *tile_start;        // [ntiles + 1]
     float hq;                     // q dt / (2 m)
     float hw0sq[3];               // (dt/2) omega0^2 per axis
-    float gdt2;                   // gamma dt / 2
+    float gdt2;                   // gamma dt / 2 (isotropic gamma)
+    float gdt2v[3];               // gamma_a dt / 2 per axis
+    int aniso;                    // bound with unequal gamma entries: the general solve
     float vF;
     float dt;
     float dtd[3];                 // dt / d_a
@@ -204,9 +206,12 @@ size_t particle_smem_bytes(const TileP &tp);
 // ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
 // variants (external field, diffuse reflection)
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext);
-// true when the launch needs the kernel with the boundary variants
+// true when the launch needs the kernel with the boundary variants (or the
+// anisotropic bound push)
 inline bool particle_launch_ext(const ParticleLaunch &pl) {
-    return pl.Eext[0] != nullptr || pl.p_diffuse > 0.f;
+    bool aniso = false;
+    for (int i = 0; i < pl.nsp; ++i) aniso = aniso || pl.sp[i].aniso;
+    return pl.Eext[0] != nullptr || pl.p_diffuse > 0.f || aniso;
 }
 
 // boundary variants (k_boundary.cu): the work-function barrier field of

@@ -172,3 +172,98 @@ def lorentz_half_space_case():
     steps = int((3 * tau + 860 * dx / I.C_LIGHT + 6 * tau + 20e-15) / dt)
     wpb2 = nb * I.QE ** 2 / (I.EPS0 * I.ME)
     return grid, mask, sp, steps, dict(dt=dt, tau=tau, dx=dx, w0=w0, gam=gam, wpb2=wpb2)
+
+# ---------------------------------------------------------------------------
+# the metal-sphere parity case shared by the GPU tests
+# ---------------------------------------------------------------------------
+
+def vel_rel(vg, vo, floor):
+    """Largest per-particle velocity difference relative to max(|v|, floor)."""
+    return np.max(np.linalg.norm(vg - vo, axis=1) / np.maximum(np.linalg.norm(vo, axis=1), floor))
+
+
+def shell_cells(mask):
+    """Material cells with a vacuum face neighbour (outside the grid counts
+    as vacuum), as linear indices."""
+    m = np.asarray(mask, bool)
+    pad = np.pad(m, 1, constant_values=False)
+    vac_nb = np.zeros_like(m)
+    for ax in range(3):
+        if m.shape[ax] == 1:
+            continue
+        for sh in (-1, 1):
+            vac_nb |= ~np.take(np.roll(pad, sh, axis=ax), range(1, m.shape[ax] + 1), axis=ax)[
+                tuple(slice(1, -1) if a != ax else slice(None) for a in range(3))]
+    return np.flatnonzero((m & vac_nb).ravel())
+
+
+def sphere_case(rng, n=(32, 28, 24), nfree=6000, nbound=3000, vscale=4e6, shell=False,
+                omega0=None, gamma=(1e14,) * 3):
+    """A metal sphere (radius 8 cells of 0.5 nm) of free and bound
+    electrons with ions at the loaded positions, CPML on every face and a
+    plane-wave source; shell=True loads the free electrons in the surface
+    shell.  omega0 defaults to 2 pi c / 400 nm on every axis."""
+    d = (0.5e-9,) * 3
+    dt = 0.5 * d[0] / (I.C_LIGHT * math.sqrt(3))
+    mask = I.sphere_mask(n, 8.0)
+    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(1, 1, 1), pml_cells=4,
+                src=dict(inc_axis=0, pol_axis=1, src_index=6, E0=3e9,
+                         omega=2 * np.pi * I.C_LIGHT / 20e-9, tau=3e-17, t0=2e-17))
+    w = 5.9e28 * d[0] ** 3 / 8
+    cells = rng.choice(shell_cells(mask), size=nfree) if shell else None
+    cell, off, v = I.random_particles(rng, n, nfree, mask=mask, vscale=vscale, cells=cells)
+    cb, anc, disp, vb = I.random_bound(rng, n, nbound, mask=mask, dscale=2e-12, vscale=2e4)
+    w0 = 2 * np.pi * I.C_LIGHT / 400e-9
+    species = [
+        dict(kind=I.FREE, q=-I.QE, m=I.ME, w=w, cell=cell, off=off, v=v, background=1),
+        dict(kind=I.BOUND, q=-I.QE, m=I.ME, w=0.5 * w, cell=cb, anchor_off=anc, disp=disp, v=vb,
+             omega0=tuple(omega0) if omega0 is not None else (w0, w0, w0), gamma=tuple(gamma),
+             background=1),
+    ]
+    return grid, mask, species
+
+
+def guarded_species(grid, mask, species, setup):
+    """Drop the free particles that end the first oracle step within 1e-5
+    cell of a face (FP32 and FP64 may cross differently there)."""
+    s = oracle_sim(grid, mask, species)
+    setup(s)
+    s.step(1)
+    Xo = s.species(0)[0]
+    s.close()
+    ok = ~near_face(Xo, grid["dims"], 1e-5)
+    assert ok.mean() > 0.99
+    keep = np.flatnonzero(ok)
+    sp0 = dict(species[0], cell=species[0]["cell"][keep], off=species[0]["off"][keep],
+               v=species[0]["v"][keep])
+    return [sp0] + list(species[1:])
+
+
+def compare_one_step(pic, h, s, grid, species):
+    """One step on both sides: velocities (1e-5 relative) and positions
+    (1e-5 cell) of species 0, velocities and displacements of the bound
+    species 1 if any, reflection count, per-cell counts (exact) and fields
+    (1e-5 relative L2).  Returns the oracle's reflection count."""
+    n = grid["n"]
+    pic.pic_step(h, 1)
+    s.step(1)
+    Xo, Vo, _, nro = s.species(0)
+    rd = pic.pic_read_species(h, 0, species[0]["cell"].size)
+    assert vel_rel(rd["v"], Vo, 1e5) < 1e-5
+    dX = periodic_delta(gpu_positions(rd, n), Xo, n, grid["dims"])
+    assert np.abs(dX).max() < 1e-5
+    if len(species) > 1:
+        Xb, Vb, Db, _ = s.species(1)
+        rb = pic.pic_read_species(h, 1, species[1]["cell"].size, bound=True)
+        assert vel_rel(rb["v"], Vb, 1e3) < 1e-5
+        assert np.abs(rb["disp"] - Db).max() < 1e-5 * np.abs(Db).max()
+    diag = pic.pic_diagnostics(h)
+    assert diag["reflections"][0] == nro
+    for k in range(len(species)):
+        assert np.array_equal(pic.pic_cell_counts(h, k, I.grid_shape(n)), s.cell_counts(k))
+    got = gpu_fields(h, grid)
+    for c in range(6):
+        ref = s.field(c)
+        if np.linalg.norm(ref) > 0:
+            assert rel_l2(got[c], ref) < 1e-5, c
+    return nro

@@ -38,10 +38,6 @@ def _pic():
     return pic
 
 
-def _vel_rel(vg, vo, floor):
-    return np.max(np.linalg.norm(vg - vo, axis=1) / np.maximum(np.linalg.norm(vo, axis=1), floor))
-
-
 # ---------------------------------------------------------------------------
 # the barrier field
 # ---------------------------------------------------------------------------
@@ -134,83 +130,6 @@ def test_boundary_variant_arguments():
 # particles against the oracle
 # ---------------------------------------------------------------------------
 
-def _shell_cells(mask):
-    """Material cells with a vacuum face neighbour (outside the grid counts
-    as vacuum), as linear indices."""
-    m = np.asarray(mask, bool)
-    pad = np.pad(m, 1, constant_values=False)
-    vac_nb = np.zeros_like(m)
-    for ax in range(3):
-        if m.shape[ax] == 1:
-            continue
-        for sh in (-1, 1):
-            vac_nb |= ~np.take(np.roll(pad, sh, axis=ax), range(1, m.shape[ax] + 1), axis=ax)[
-                tuple(slice(1, -1) if a != ax else slice(None) for a in range(3))]
-    return np.flatnonzero((m & vac_nb).ravel())
-
-
-def _sphere_case(rng, n=(32, 28, 24), nfree=6000, nbound=3000, vscale=4e6, shell=False):
-    d = (0.5e-9,) * 3
-    dt = 0.5 * d[0] / (I.C_LIGHT * math.sqrt(3))
-    mask = I.sphere_mask(n, 8.0)
-    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(1, 1, 1), pml_cells=4,
-                src=dict(inc_axis=0, pol_axis=1, src_index=6, E0=3e9,
-                         omega=2 * np.pi * I.C_LIGHT / 20e-9, tau=3e-17, t0=2e-17))
-    w = 5.9e28 * d[0] ** 3 / 8
-    cells = rng.choice(_shell_cells(mask), size=nfree) if shell else None
-    cell, off, v = I.random_particles(rng, n, nfree, mask=mask, vscale=vscale, cells=cells)
-    cb, anc, disp, vb = I.random_bound(rng, n, nbound, mask=mask, dscale=2e-12, vscale=2e4)
-    w0 = 2 * np.pi * I.C_LIGHT / 400e-9
-    species = [
-        dict(kind=I.FREE, q=-I.QE, m=I.ME, w=w, cell=cell, off=off, v=v, background=1),
-        dict(kind=I.BOUND, q=-I.QE, m=I.ME, w=0.5 * w, cell=cb, anchor_off=anc, disp=disp, v=vb,
-             omega0=(w0, w0, w0), gamma=(1e14,) * 3, background=1),
-    ]
-    return grid, mask, species
-
-
-def _guarded(grid, mask, species, setup):
-    """Drop the free particles that end the first oracle step within 1e-5
-    cell of a face (FP32 and FP64 may cross differently there)."""
-    s = PR.oracle_sim(grid, mask, species)
-    setup(s)
-    s.step(1)
-    Xo = s.species(0)[0]
-    s.close()
-    ok = ~PR.near_face(Xo, grid["dims"], 1e-5)
-    assert ok.mean() > 0.99
-    keep = np.flatnonzero(ok)
-    sp0 = dict(species[0], cell=species[0]["cell"][keep], off=species[0]["off"][keep],
-               v=species[0]["v"][keep])
-    return [sp0] + list(species[1:])
-
-
-def _compare_one_step(pic, h, s, grid, species):
-    n = grid["n"]
-    pic.pic_step(h, 1)
-    s.step(1)
-    Xo, Vo, _, nro = s.species(0)
-    rd = pic.pic_read_species(h, 0, species[0]["cell"].size)
-    assert _vel_rel(rd["v"], Vo, 1e5) < 1e-5
-    dX = PR.periodic_delta(PR.gpu_positions(rd, n), Xo, n, grid["dims"])
-    assert np.abs(dX).max() < 1e-5
-    if len(species) > 1:
-        Xb, Vb, Db, _ = s.species(1)
-        rb = pic.pic_read_species(h, 1, species[1]["cell"].size, bound=True)
-        assert _vel_rel(rb["v"], Vb, 1e3) < 1e-5
-        assert np.abs(rb["disp"] - Db).max() < 1e-5 * np.abs(Db).max()
-    diag = pic.pic_diagnostics(h)
-    assert diag["reflections"][0] == nro
-    for k in range(len(species)):
-        assert np.array_equal(pic.pic_cell_counts(h, k, I.grid_shape(n)), s.cell_counts(k))
-    got = PR.gpu_fields(h, grid)
-    for c in range(6):
-        ref = s.field(c)
-        if np.linalg.norm(ref) > 0:
-            assert PR.rel_l2(got[c], ref) < 1e-5, c
-    return nro
-
-
 @pytest.mark.parametrize("overlap,mode", [(1, 2), (0, 2), (1, 1), (0, 3)])
 def test_potential_wall_matches_oracle(overlap, mode):
     """The potential-wall surface: open edges plus the work-function barrier
@@ -219,14 +138,14 @@ def test_potential_wall_matches_oracle(overlap, mode):
     after 30 more steps the fields match to 1e-3 and some electrons have left
     the sphere (open edges) with no material-edge reflection."""
     rng = np.random.default_rng(51)
-    grid, mask, species = _sphere_case(rng)
+    grid, mask, species = PR.sphere_case(rng)
     W = 4.3
 
     def setup(s):
         s.set_external_field(s.work_function_field(W))
         s.set_particle_bc(open_edges=True)
 
-    species = _guarded(grid, mask, species, setup)
+    species = PR.guarded_species(grid, mask, species, setup)
     pic = _pic()
     s = PR.oracle_sim(grid, mask, species)
     setup(s)
@@ -234,7 +153,7 @@ def test_potential_wall_matches_oracle(overlap, mode):
     pic.pic_set_work_function(h, W)
     pic.pic_set_particle_bc(h, pic.PIC_EDGE_OPEN)
     try:
-        nro = _compare_one_step(pic, h, s, grid, species)
+        nro = PR.compare_one_step(pic, h, s, grid, species)
         assert nro == 0
         pic.pic_step(h, 30)
         s.step(30)
@@ -263,20 +182,20 @@ def test_diffuse_reflection_matches_oracle(overlap, p):
     one step; after 20 more steps 99 % of the velocities agree to 1e-4 and
     every electron is still in the metal."""
     rng = np.random.default_rng(52)
-    grid, mask, species = _sphere_case(rng, vscale=2e7, shell=True)
+    grid, mask, species = PR.sphere_case(rng, vscale=2e7, shell=True)
     seed = 0x1234_5678_9ABC
 
     def setup(s):
         s.set_particle_bc(p_diffuse=p, seed=seed)
 
-    species = _guarded(grid, mask, species, setup)
+    species = PR.guarded_species(grid, mask, species, setup)
     pic = _pic()
     s = PR.oracle_sim(grid, mask, species)
     setup(s)
     h = PR.gpu_sim(grid, mask, species, tuning=dict(no_overlap=1 - overlap, field_mode=2))
     pic.pic_set_particle_bc(h, pic.PIC_EDGE_REFLECT, p, seed)
     try:
-        nro = _compare_one_step(pic, h, s, grid, species)
+        nro = PR.compare_one_step(pic, h, s, grid, species)
         assert nro > 40
         pic.pic_step(h, 20)
         s.step(20)
@@ -305,7 +224,7 @@ def test_diffuse_dirac_disk_matches_oracle():
     vF = 3e7  # fast enough that many carriers meet the edge within a few steps
     m_d = (0.2 * I.QE / 1e6) / (2 * 1e6)
     cell, off, _ = I.random_particles(rng, n, 8000, mask=mask, dims=2,
-                                      cells=rng.choice(_shell_cells(mask), size=8000))
+                                      cells=rng.choice(PR.shell_cells(mask), size=8000))
     phi = rng.uniform(0, 2 * np.pi, cell.size)
     v = np.stack([vF * np.cos(phi), vF * np.sin(phi), np.zeros_like(phi)], 1).astype(np.float32)
     w = 1e25 * np.prod(d) / 32
@@ -316,14 +235,14 @@ def test_diffuse_dirac_disk_matches_oracle():
     def setup(s):
         s.set_particle_bc(p_diffuse=1.0, seed=seed)
 
-    species = _guarded(grid, mask, species, setup)
+    species = PR.guarded_species(grid, mask, species, setup)
     pic = _pic()
     s = PR.oracle_sim(grid, mask, species)
     setup(s)
     h = PR.gpu_sim(grid, mask, species)
     pic.pic_set_particle_bc(h, pic.PIC_EDGE_REFLECT, 1.0, seed)
     try:
-        nro = _compare_one_step(pic, h, s, grid, species)
+        nro = PR.compare_one_step(pic, h, s, grid, species)
         assert nro > 20
         pic.pic_step(h, 29)
         s.step(29)
@@ -342,7 +261,7 @@ def test_zero_external_field_changes_nothing():
     variants but adds exact zeros: velocities after one step are bit-equal to
     the plain kernel's."""
     rng = np.random.default_rng(54)
-    grid, mask, species = _sphere_case(rng, nfree=4000, nbound=2000)
+    grid, mask, species = PR.sphere_case(rng, nfree=4000, nbound=2000)
     pic = _pic()
     h0 = PR.gpu_sim(grid, mask, species)
     h1 = PR.gpu_sim(grid, mask, species)

@@ -390,7 +390,7 @@ def test_abi_rejects_bad_arguments():
     h = pic.pic_create(g)
     try:
         bad = pic.species_desc(pic.PIC_BOUND, -I.QE, I.ME, 1.0, omega0=(1e15,) * 3,
-                               gamma=(1e14, 2e14, 1e14))
+                               gamma=(1e14, -2e14, 1e14))
         with pytest.raises(pic.PicError):
             pic.pic_load_species(h, bad, cell=np.zeros(1, np.int32),
                                  anchor_off=np.zeros((1, 3)), v=np.zeros((1, 3), np.float32))

@@ -33,6 +33,12 @@ MUTATIONS = [
      "test_bound_push_reproduces_taflove_recurrence"),
     ("damping sign", "rhs[r] = (1.0 - 0.5 * dt * gamma[r]) * vm[r];",
      "rhs[r] = (1.0 + 0.5 * dt * gamma[r]) * vm[r];", "test_bound_damping_factor"),
+    ("damping of the wrong axis", "rhs[r] = (1.0 - 0.5 * dt * gamma[r]) * vm[r];",
+     "rhs[r] = (1.0 - 0.5 * dt * gamma[(r + 1) % 3]) * vm[r];", "test_bound_anisotropic_gamma"),
+    ("damping of the wrong axis in the solve",
+     "L[r][c] = (r == c ? 1.0 + 0.5 * dt * gamma[r] : 0.0) - X[r][c];",
+     "L[r][c] = (r == c ? 1.0 + 0.5 * dt * gamma[2 - r] : 0.0) - X[r][c];",
+     "test_bound_anisotropic_gamma"),
     ("reflection not mirrored", "X1[a] = 2.0 * face - X1[a];", "X1[a] = X0[a];",
      "test_reflection_hand_computed"),
     ("source sign", "double Js = -2.0 * s->E0", "double Js = 2.0 * s->E0",

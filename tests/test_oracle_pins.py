@@ -226,6 +226,42 @@ def test_bound_driven_amplitude_matches_discrete_closed_form():
     assert abs(X / cont - 1) < 0.01
 
 
+def test_bound_anisotropic_gamma():
+    """Diagonal damping gamma = (g_x, g_y, g_z) (the general 3x3 solve).
+    With B = 0 the axes decouple and each follows Eq. taflove with its own
+    w0 and gamma; with B the rotation step keeps the discrete energy balance
+    |v+|^2 - |v-|^2 = -sum_a g_a dt/2 (v+_a + v-_a)^2 (the magnetic term
+    does no work), v- and v+ the velocities around it."""
+    q, m, dt = -QE, ME, 4.81e-19
+    w0 = np.array([4.7e15, 3.1e15, 6.0e15])
+    g = np.array([1e14, 4e14, 2.5e13])
+    v, D = np.zeros(3), np.zeros(3)
+    xs, Es = [D.copy()], []
+    for n in range(400):
+        E = RNG.normal(size=3) * 1e9
+        Es.append(E)
+        v, D = O.push_bound(v, D, E, np.zeros(3), q, m, dt, w0, g)
+        xs.append(D.copy())
+    xs = np.array(xs)
+    for n in range(1, 399):
+        lhs = xs[n + 1] - 2 * xs[n] + xs[n - 1]
+        rhs = dt * dt * (q / m * Es[n] - w0 ** 2 * xs[n] - g * (xs[n + 1] - xs[n - 1]) / (2 * dt))
+        scale = dt * dt * np.abs(q / m * Es[n]).max()
+        assert np.all(np.abs(lhs - rhs) < 1e-9 * scale)
+    # energy balance of the rotation step: E = 0 and D = 0 make the two
+    # kicks vanish, so v- = v and v+ = the pushed v
+    dt2 = 1e-16
+    g2 = np.array([3e14, 1e13, 8e14])
+    for _ in range(50):
+        v0 = RNG.normal(size=3) * 1e6
+        B = RNG.normal(size=3) * 2e3
+        v1, _ = O.push_bound(v0, np.zeros(3), np.zeros(3), B, q, m, dt2, [0] * 3, g2)
+        lhs = v1 @ v1 - v0 @ v0
+        rhs = -np.sum(g2 * dt2 / 2 * (v1 + v0) ** 2)
+        assert abs(lhs - rhs) < 1e-12 * (v0 @ v0)
+        assert abs(rhs) > 1e-4 * (v0 @ v0)
+
+
 def test_bound_push_reduces_to_boris_when_unbound():
     """gamma = 0, w0 = 0: the gyrotropic solve equals the Boris rotation."""
     q, m, dt = -QE, ME, 1e-16
