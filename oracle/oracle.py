@@ -84,6 +84,8 @@ def _declare(L):
     L.orc_species_count.argtypes = [C.c_void_p, C.c_int]
     L.orc_get_species.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp, _i64p]
     L.orc_cell_counts.argtypes = [C.c_void_p, C.c_int, _i32p]
+    L.orc_energy_histogram.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int,
+                                       C.POINTER(C.c_uint64)]
     L.orc_diag.argtypes = [C.c_void_p, _dp]
     L.orc_rho.argtypes = [C.c_void_p, _dp]
     L.orc_gather.argtypes = [C.c_void_p, _dp, _dp, _dp]
@@ -328,6 +330,14 @@ class OracleSim:
     def cell_counts(self, k):
         out = np.zeros(self.shape, dtype=np.int32)
         lib().orc_cell_counts(self._h, k, out.ctypes.data_as(_i32p))
+        return out
+
+    def energy_histogram(self, k, e_max, nbins):
+        """Kinetic-energy histogram of species k: nbins bins of width
+        e_max / nbins, then the count of E >= e_max (uint64, nbins + 1)."""
+        out = np.zeros(nbins + 1, dtype=np.uint64)
+        lib().orc_energy_histogram(self._h, k, float(e_max), int(nbins),
+                                   out.ctypes.data_as(C.POINTER(C.c_uint64)))
         return out
 
     def rho(self):

@@ -887,6 +887,30 @@ void orc_get_species(void *h, int k, double *X, double *V, double *D, long long 
     *nrefl = sp->nrefl;
 }
 
+/* Histogram of the kinetic energy E = m |v|^2 / 2 of species k's particles
+   (the relaxation study of Sec. 2 fits the high-energy tail of this
+   histogram): out[b], b < nbins, counts E in [b D, (b+1) D), D = e_max /
+   nbins; out[nbins] counts E >= e_max.  E is formed as
+   0.5 m ((vx vx + vy vy) + vz vz) and the bin as floor(E / D), each
+   operation rounded once. */
+void orc_energy_histogram(void *h, int k, double e_max, int nbins, uint64_t *out) {
+    orc_sim *s = (orc_sim *)h;
+    orc_species *sp = &s->sp[k];
+    const double D = e_max / nbins;
+    memset(out, 0, (size_t)(nbins + 1) * sizeof(uint64_t));
+    for (long p = 0; p < sp->n; ++p) {
+        const double *v = &sp->V[3 * p];
+        double E = 0.5 * sp->m * ((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+        long b;
+        if (E >= e_max) b = nbins;
+        else {
+            b = (long)floor(E / D);
+            if (b > nbins - 1) b = nbins - 1;
+        }
+        out[b] += 1;
+    }
+}
+
 /* Particles per cell (cell of the current position), x fastest. */
 void orc_cell_counts(void *h, int k, int32_t *out) {
     orc_sim *s = (orc_sim *)h;

@@ -81,6 +81,10 @@ MUTATIONS = [
     ("2D law uniform in angle", "const double st = 2.0 * u1 - 1.0, ct = sqrt(1.0 - st * st);",
      "const double st = sin(PI * (u1 - 0.5)), ct = sqrt(1.0 - st * st);",
      "test_diffuse_reflection_of_dirac_carriers_is_2d_lambert"),
+    ("histogram edge", "if (E >= e_max) b = nbins;", "if (E > e_max) b = nbins;",
+     "test_energy_histogram_bin_edges"),
+    ("histogram energy factor", "double E = 0.5 * sp->m * ((v[0] * v[0]",
+     "double E = sp->m * ((v[0] * v[0]", "test_energy_histogram_of_the_T0_fermi_sea"),
 ]
 
 

@@ -1024,3 +1024,42 @@ def test_diffuse_fraction_and_draw_layout():
         want[j] = (int(w[0]) >> 8) / 16777216.0 < float(np.float32(p))
     assert np.array_equal(diffuse, want)
     assert abs(diffuse.mean() - p) < 4 * math.sqrt(p * (1 - p) / N)
+
+
+# ---------------------------------------------------------------------------
+# kinetic-energy histogram (the relaxation study of Sec. 2)
+# ---------------------------------------------------------------------------
+
+def test_energy_histogram_bin_edges():
+    """Hand-computed: m = 2 kg, so E = |v|^2 J; bins of width 1 J up to 4 J,
+    half-open [b, b+1), E >= 4 J in the overflow entry."""
+    s = O.OracleSim(dims=3, n=(4, 4, 4), d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
+    V = [[0, 0, 0], [1, 0, 0], [1, 1, 1], [2, 0, 0], [0, 1.9999, 0], [0, 0, 1.5],
+         [1, 1, 0], [3, 0, 0], [0.5, 0.5, 0.5]]
+    # E = 0, 1, 3, 4, 3.9996, 2.25, 2, 9, 0.75
+    s.add_species(O.KIND_FREE, -QE, 2.0, 1.0, [[1.5, 1.5, 1.5]] * len(V), V)
+    h = s.energy_histogram(0, 4.0, 4)
+    assert h.tolist() == [2, 1, 2, 2, 2]
+
+
+def test_energy_histogram_of_the_T0_fermi_sea():
+    """The T = 0 loader fills the Fermi sphere uniformly, so the fraction of
+    particles with E < x is (x / E_F)^(3/2): every bin holds
+    N ((b / E_F)^1.5 - (a / E_F)^1.5) within 4.5 sigma, nothing lies above
+    E_F, and the counts sum to N."""
+    EF = 5.53 * QE
+    n = (12, 12, 12)
+    cell, off, v = O.fd_load(3, n, None, O.KIND_FREE, ME, EF, 0.0, 0.0, 64, False, 17, 0)
+    X = np.column_stack(np.unravel_index(cell, (n[2], n[1], n[0]))[::-1]) + off
+    s = O.OracleSim(dims=3, n=n, d=(0.2e-9,) * 3, dt=1e-19, bc=(0, 0, 0))
+    s.add_species(O.KIND_FREE, -QE, ME, 1.0, X, v)
+    N = len(cell)
+    nb = 24
+    h = s.energy_histogram(0, 1.2 * EF, nb).astype(np.int64)
+    assert h.sum() == N
+    edges = np.linspace(0, 1.2, nb + 1)
+    cdf = np.minimum(edges, 1.0) ** 1.5
+    want = N * np.diff(cdf)
+    assert np.all(h[:nb][edges[1:] > 1.0 + 1e-12] == 0) and h[nb] == 0
+    inside = edges[1:] <= 1.0 + 1e-12
+    assert np.all(np.abs(h[:nb][inside] - want[inside]) <= 4.5 * np.sqrt(want[inside]) + 1)
