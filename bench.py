@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-graphene", action="store_true", help="skip the graphene-sheet leg")
+    ap.add_argument("--no-relax", action="store_true", help="skip the FD relaxation leg")
+    ap.add_argument("--relax-fs", type=float, default=20.0, help="FD relaxation run length (fs)")
     ap.add_argument("--graphene-steps", type=int, default=200)
     ap.add_argument("--batch-sims", type=int, default=256)
     ap.add_argument("--serve-jobs", type=int, default=24)
@@ -356,9 +358,11 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu, fp64 = cpu_baseline_and_error(pic, I, wl, stream)
     pic.pic_destroy(h)
-    batch = serve = graphene = None
+    batch = serve = graphene = relaxation = None
     if rank == 0 and not args.no_graphene:
         graphene = run_graphene_leg(args, pic, I, stream, peak)
+    if rank == 0 and not args.no_relax:
+        relaxation = run_relax_leg(args)
     if not args.no_batch:
         batch = run_batch_leg(args, rank, world)
     if rank == 0 and not args.no_serve:
@@ -390,7 +394,7 @@ def run_gpu(args):
         "step_roofline_note": "minimal step bytes: fused field update (48 B/cell + CPML + J) + "
                               "particle bytes, whatever the field mode",
         "cpu_baseline": cpu, "e2e": e2e, "fp64_error": fp64, "batch": batch, "serve": serve,
-        "graphene": graphene,
+        "graphene": graphene, "relaxation": relaxation,
         "clocks": clk.summary(), "gpu_launches": int(tm["kernel_launches"]),
         "gpu_launches_per_step": launches_per_step,
     }
@@ -453,6 +457,33 @@ def run_batch_leg(args, rank=0, world=1):
                            tuning={"tile": list(s_tun["tile"]),
                                    "sort_interval": s_tun["sort_interval"]}),
             "speedup_vs_serial": s["seconds"] / b["seconds"]}
+
+
+def run_relax_leg(args):
+    """The Fermi-Dirac relaxation study of Sec. 2 as a second workload: 2 nm
+    periodic cubes of bulk electrons (2, 4, 6 x 1e28 m^-3; 16, 32, 64, 128
+    ppc; 12 simulations, 720 k particles) advanced together by the batch
+    engine for 20 fs; the tail temperature beta(t) of each, its fit
+    beta = A sqrt(t), and the whole job's particle-steps / s (histogram
+    readbacks between chunks are outside the timed group steps)."""
+    from paper_2501_07465_gb300 import relax
+    r = relax.run(t_end_fs=args.relax_fs, samples=20)
+    return {"workload": "FD relaxation: 2 nm periodic bulk cubes, 0.2 nm cells, T0 = 0.0375 eV, "
+                        "n = 2/4/6e28 m^-3 x 16/32/64/128 ppc, one batch group",
+            "steps": r["steps"], "t_end_fs": args.relax_fs, "tile": r["tile"],
+            "wall_s": r["wall_s"], "particle_steps_per_s": r["particle_steps_per_s"],
+            "ms_per_step": 1e3 * r["wall_s"] / r["steps"],
+            "note": "beta0 is null where the loading tail holds too few particles to fit",
+            "cases": [{"density": c["density"], "ppc": c["ppc"], "particles": c["particles"],
+                       "A_eV_per_sqrt_fs": finite(c["A_eV_per_sqrt_fs"], 5),
+                       "r2": finite(c["r2"], 4), "beta0_eV": finite(c["beta_eV"][0], 5),
+                       "beta_end_eV": finite(c["beta_eV"][-1], 5)}
+                      for c in r["cases"]]}
+
+
+def finite(x, nd):
+    """x rounded, or None where it is not finite (the JSON line stays strict)."""
+    return round(float(x), nd) if math.isfinite(x) else None
 
 
 def run_graphene_leg(args, pic, I, stream, peak):

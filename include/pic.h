@@ -305,6 +305,17 @@ pic_status pic_cell_counts(pic_sim *sim, int species, int32_t *host_out, size_t 
 /* FP64 diagnostics (kinetic and field energy, Gauss residual, counts). */
 pic_status pic_diagnostics(pic_sim *sim, pic_diag *out);
 
+/* Histogram of the kinetic energy E = m |v|^2 / 2 of one species'
+   macro-particles (the relaxation study of Sec. 2 fits its high-energy
+   tail): host_out[b], b < nbins, counts E in [b D, (b+1) D) with
+   D = e_max / nbins; host_out[nbins] counts E >= e_max.  E is formed in FP64
+   from the FP32 velocities as (0.5 m) ((vx vx + vy vy) + vz vz) and the bin
+   as floor(E / D), each operation rounded once, so for given velocities the
+   counts are exact.  nbins 1 .. 2^20, e_max finite and > 0,
+   n = nbins + 1 (PIC_EINVAL otherwise).  Synchronous. */
+pic_status pic_energy_histogram(pic_sim *sim, int species, double e_max, int nbins,
+                                uint64_t *host_out, size_t n);
+
 /* Kernel timing totals since the last call; resets them.  Synchronous. */
 pic_status pic_get_timing(pic_sim *sim, pic_timing *out);
 

@@ -1,5 +1,6 @@
 // k_diag.cu -- FP64 diagnostic reductions (kinetic and field energy, the
-// Gauss-law residual div E - rho/eps0 on the Yee nodes) and the copy helpers
+// Gauss-law residual div E - rho/eps0 on the Yee nodes, the kinetic-energy
+// histogram of the relaxation study of Sec. 2) and the copy helpers
 // used by the ABI (un-sorting particles back to load order, layout and
 // precision conversions).
 #include <math.h>
@@ -54,6 +55,39 @@ __global__ void kinetic_kernel(SpeciesP sp, double mw_half, double *acc) {
     }
     s = block_sum(s);
     if (threadIdx.x == 0) atomicAdd(acc, s * mw_half);
+}
+
+// Kinetic-energy histogram (the relaxation study of Sec. 2): E in FP64 from
+// the FP32 velocities as half_m ((vx vx + vy vy) + vz vz), bin floor(E / D),
+// every operation rounded once (no contraction), so the counts are exact
+// for given velocities.  Block-private counters in shared memory when
+// `priv` (nbins + 1 of them fit), global atomics otherwise.
+__global__ void energy_hist_kernel(SpeciesP sp, double half_m, double e_max, double D, int nbins,
+                                   int priv, unsigned long long *out) {
+    extern __shared__ unsigned int hist[];
+    if (priv) {
+        for (int b = threadIdx.x; b <= nbins; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+    }
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < sp.n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const double a = sp.v[0][p], b = sp.v[1][p], c = sp.v[2][p];
+        const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+        const double E = __dmul_rn(half_m, v2);
+        int bin;
+        if (E >= e_max) bin = nbins;
+        else {
+            const double f = floor(__ddiv_rn(E, D));
+            bin = f > (double)(nbins - 1) ? nbins - 1 : (int)f;
+        }
+        if (priv) atomicAdd(&hist[bin], 1u);
+        else atomicAdd(&out[bin], 1ull);
+    }
+    if (priv) {
+        __syncthreads();
+        for (int b = threadIdx.x; b <= nbins; b += blockDim.x)
+            if (hist[b]) atomicAdd(&out[b], (unsigned long long)hist[b]);
+    }
 }
 
 __global__ void field_energy_kernel(long long n, const float *E0, const float *E1, const float *E2,
@@ -215,6 +249,17 @@ __global__ void f64_to_f32_kernel(const double *in, float *out, long long n) {
 cudaError_t launch_kinetic(const SpeciesP &sp, double mw_half, double *acc, cudaStream_t s) {
     if (sp.n <= 0) return cudaSuccess;
     kinetic_kernel<<<blocks_for(sp.n), 256, 0, s>>>(sp, mw_half, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_histogram(const SpeciesP &sp, double half_m, double e_max, int nbins,
+                                    unsigned long long *out, cudaStream_t s) {
+    if (sp.n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(nbins + 1) * sizeof(unsigned int);
+    const int priv = smem <= 32 * 1024;
+    const double D = e_max / nbins;
+    energy_hist_kernel<<<blocks_for(sp.n), 256, priv ? smem : 0, s>>>(sp, half_m, e_max, D, nbins,
+                                                                      priv, out);
     return cudaGetLastError();
 }
 

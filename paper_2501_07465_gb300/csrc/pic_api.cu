@@ -1058,6 +1058,25 @@ pic_status pic_cell_counts(pic_sim *s, int k, int32_t *out, size_t n) {
     return check_device_status(s);
 }
 
+pic_status pic_energy_histogram(pic_sim *s, int k, double e_max, int nbins, uint64_t *out,
+                                size_t n) {
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
+    if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
+    if (k < 0 || k >= s->nsp) return fail(s, PIC_EINVAL, "no such species");
+    if (nbins < 1 || nbins > (1 << 20)) return fail(s, PIC_EINVAL, "nbins must be 1 .. 2^20");
+    if (!(e_max > 0.0 && e_max < 1e300)) return fail(s, PIC_EINVAL, "e_max must be finite and > 0");
+    if (n != (size_t)nbins + 1) return fail(s, PIC_EINVAL, "n must equal nbins + 1");
+    unsigned long long *d = nullptr;
+    if (!alloc_zero(s, &d, n)) return fail(s, PIC_ENOMEM, "histogram");
+    Species &sp = s->sp[k];
+    CK(s, launch_energy_histogram(species_params(s, sp, sp.cur), 0.5 * sp.desc.m, e_max, nbins, d,
+                                  s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    CK(s, cudaMemcpy(out, d, n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    dfree(s, d);
+    return check_device_status(s);
+}
+
 pic_status pic_diagnostics(pic_sim *s, pic_diag *out) {
     if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");

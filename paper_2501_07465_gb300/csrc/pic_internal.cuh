@@ -284,6 +284,8 @@ struct DiagAcc {
     double gauss_sum2;
 };
 cudaError_t launch_kinetic(const SpeciesP &sp, double mw_half, double *acc, cudaStream_t s);
+cudaError_t launch_energy_histogram(const SpeciesP &sp, double half_m, double e_max, int nbins,
+                                    unsigned long long *out, cudaStream_t s);
 cudaError_t launch_field_energy(const GridP &g, const float *const *E, const float *const *B,
                                 DiagAcc *acc, cudaStream_t s);
 cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V,

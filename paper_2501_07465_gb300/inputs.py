@@ -227,6 +227,31 @@ def graphene3d(nx=512, ny=512, nz=64, ppc=32, steps=2000, pml=16):
     }
 
 
+def fermi_energy(n, m=ME):
+    """E_F = hbar^2 / (2 m) (3 pi^2 n)^(2/3) (Sec. 2, exponent read as 2/3)."""
+    return HBAR ** 2 / (2 * m) * (3 * math.pi ** 2 * n) ** (2.0 / 3.0)
+
+
+def bulk_cube(n_e, ppc, side_nm=2.0, cell_nm=0.2, T_eV=0.0375, steps=104000, seed=SEED_BASE + 5):
+    """The Fermi-Dirac relaxation workload (Sec. 2): a periodic cube of bulk
+    electron plasma, side 2 nm, fixed uniform ions, electrons placed at
+    random with FD momenta at T = 0.0375 eV and E_F from the density.  The
+    cell (0.2 nm) and the run length (104000 steps = 20 fs at 0.5 x CFL) are
+    chosen here: the paper's supplementary parameters are not given."""
+    n = int(round(side_nm / cell_nm))
+    dx = cell_nm * 1e-9
+    dt = 0.5 * dx / (C_LIGHT * math.sqrt(3))
+    return {
+        "name": f"bulk cube {side_nm}nm n={n_e:.1e} {ppc}ppc",
+        "grid": dict(dims=3, n=(n, n, n), d=(dx, dx, dx), dt=dt, bc=(0, 0, 0), pml_cells=0),
+        "mask": None,
+        "species": [dict(kind=FREE, q=-QE, m=ME, density=n_e, E_F=fermi_energy(n_e),
+                         T=T_eV * QE / 1.380649e-23, ppc=ppc, quiet=0, background=2,
+                         seed=seed, stream=0)],
+        "steps": steps,
+    }
+
+
 # ---------------------------------------------------------------------------
 # batched sweep and served job stream
 # ---------------------------------------------------------------------------

@@ -110,6 +110,8 @@ SIGNATURES = {
                                    C.POINTER(C.c_float), C.c_size_t]),
     "pic_cell_counts": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int32), C.c_size_t]),
     "pic_diagnostics": (C.c_int, [_H, C.POINTER(pic_diag)]),
+    "pic_energy_histogram": (C.c_int, [_H, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_uint64),
+                                       C.c_size_t]),
     "pic_get_timing": (C.c_int, [_H, C.POINTER(pic_timing)]),
     "pic_memory_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "pic_last_error": (C.c_char_p, [_H]),
@@ -362,6 +364,15 @@ def pic_cell_counts_noalloc(h, k, shape):
     PIC_NOALLOC_MAX_CELLS cells; larger grids raise PicError)."""
     out = np.zeros(tuple(shape), np.int32)
     _check(load_library().pic_cell_counts_noalloc(h, k, _ptr(out, C.c_int32), out.size), h)
+    return out
+
+
+def pic_energy_histogram(h, k, e_max, nbins):
+    """Kinetic-energy histogram of species k (uint64, nbins + 1: nbins bins
+    of width e_max / nbins, then the count of E >= e_max)."""
+    out = np.zeros(int(nbins) + 1, dtype=np.uint64)
+    _check(load_library().pic_energy_histogram(h, int(k), float(e_max), int(nbins),
+                                               _ptr(out, C.c_uint64), out.size), h)
     return out
 
 

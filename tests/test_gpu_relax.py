@@ -1,0 +1,129 @@
+"""GPU parity of the relaxation study's pieces (Sec. 2): the kinetic-energy
+histogram (integer work: bit-exact against the oracle on the same
+velocities), the tail temperature at loading against the Fermi-Dirac law,
+and the numerical heating of a bulk cube against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2501_07465_gb300 import inputs as I
+
+from tests import pairs as PR
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+def _pic():
+    from paper_2501_07465_gb300 import pic
+    return pic
+
+
+@pytest.mark.parametrize("nbins", [500, 20000])
+def test_energy_histogram_matches_oracle_exactly(nbins):
+    """Same FP32 velocities on both sides: identical counts, for the
+    shared-memory (500 bins) and the global-atomic (20000 bins) kernels;
+    some energies land above e_max."""
+    pic = _pic()
+    rng = np.random.default_rng(71)
+    n = (16, 12, 10)
+    grid = dict(dims=3, n=n, d=(0.2e-9,) * 3, dt=1e-19, bc=(0, 0, 0))
+    cell, off, v = I.random_particles(rng, n, 200000, vscale=9e5)
+    species = [dict(kind=I.FREE, q=-I.QE, m=I.ME, w=1.0, cell=cell, off=off, v=v)]
+    e_max = 8.0 * I.QE
+    s = PR.oracle_sim(grid, None, species)
+    h = PR.gpu_sim(grid, None, species)
+    try:
+        got = pic.pic_energy_histogram(h, 0, e_max, nbins)
+        want = s.energy_histogram(0, e_max, nbins)
+        assert got.sum() == cell.size and want[-1] > 0
+        assert np.array_equal(got, want)
+        for bad in ((0.0, nbins), (float("nan"), nbins), (e_max, 0), (e_max, 1 << 21)):
+            with pytest.raises(pic.PicError) as e:
+                pic.pic_energy_histogram(h, 0, *bad)
+            assert e.value.status == pic.PIC_EINVAL
+    finally:
+        pic.pic_destroy(h)
+        s.close()
+
+
+def _fd_tail_expectation(EF, kT, N, e_max, nbins, e_lo):
+    """Counts of the 3D FD energy law sqrt(E) / (1 + exp((E - E_F) / kT))
+    per bin (fine trapezoid sums), scaled to N, and their tail fit."""
+    from paper_2501_07465_gb300 import relax
+    E = np.linspace(0, e_max, nbins * 64 + 1)
+    dens = np.sqrt(E) / (1 + np.exp(np.clip((E - EF) / kT, -700, 700)))
+    cum = np.concatenate([[0], np.cumsum(0.5 * (dens[1:] + dens[:-1]) * np.diff(E))])
+    per_bin = np.diff(cum[::64])
+    counts = np.append(N * per_bin / cum[-1], 0)
+    return relax.tail_beta(counts, e_max, e_lo)[0]
+
+
+def test_tail_temperature_at_loading():
+    """The device FD loader at T = 0.0375 eV, 128 ppc in a 4 nm cube
+    (1.02 M electrons at 6e28 m^-3): the tail fit of its histogram (bins of
+    0.37 kT) equals the fit of the exact FD energy law on the same bins
+    within 12 % (3.5 sigma of the fit's Poisson spread, 3.4 %)."""
+    from paper_2501_07465_gb300 import relax, runner
+    pic = _pic()
+    wl = I.bulk_cube(6e28, 128, side_nm=4.0)
+    h = runner.make_sim(wl)
+    try:
+        EF = wl["species"][0]["E_F"]
+        kT = 0.0375 * I.QE
+        N = int(pic.pic_diagnostics(h)["count"][0])
+        e_max, nbins, e_lo = 3 * EF, 1200, EF + 2 * kT
+        beta = relax.tail_beta(pic.pic_energy_histogram(h, 0, e_max, nbins), e_max, e_lo)[0]
+        want = _fd_tail_expectation(EF, kT, N, e_max, nbins, e_lo)
+        assert abs(beta / want - 1) < 0.12, (beta / I.QE, want / I.QE)
+    finally:
+        pic.pic_destroy(h)
+
+
+def test_relaxation_heating_matches_oracle():
+    """A 1.2 nm bulk cube (6^3 cells of 0.2 nm, 32 ppc FD electrons at
+    6e28 m^-3, T0 = 0.0375 eV, fixed uniform ions) loaded on the device and
+    handed to the oracle particle by particle: after 2600 steps (0.5 fs) the
+    tail temperature (bins of 56 meV) has grown beyond ten times T0 on both
+    sides and agrees within 15 %, and the kinetic energy within 2 %."""
+    from paper_2501_07465_gb300 import relax, runner
+    pic = _pic()
+    wl = I.bulk_cube(6e28, 32)
+    wl["grid"]["n"] = (6, 6, 6)
+    h = runner.make_sim(wl, 0, dict(tile=(2, 2, 2)))
+    grid = wl["grid"]
+    n = grid["n"]
+    EF = wl["species"][0]["E_F"]
+    kT = 0.0375 * I.QE
+    N = int(pic.pic_diagnostics(h)["count"][0])
+    rd = pic.pic_read_species(h, 0, N)
+    w = wl["species"][0]["density"] * np.prod(grid["d"]) / 32
+    s = O.OracleSim(**grid)
+    s.add_species(O.KIND_FREE, -I.QE, I.ME, w, PR.gpu_positions(rd, n),
+                  rd["v"].astype(np.float64), bg=2)
+    e_max, nbins, e_lo = 3 * EF, 300, EF + 2 * kT
+    try:
+        pic.pic_step(h, 2600)
+        s.step(2600)
+        bg = relax.tail_beta(pic.pic_energy_histogram(h, 0, e_max, nbins), e_max, e_lo)[0]
+        bo = relax.tail_beta(s.energy_histogram(0, e_max, nbins), e_max, e_lo)[0]
+        assert bg > 10 * kT and bo > 10 * kT
+        assert abs(bg / bo - 1) < 0.15, (bg / I.QE, bo / I.QE)
+        kg = pic.pic_diagnostics(h)["kinetic"][0]
+        ko = s.diag()["kinetic"][0]
+        assert abs(kg / ko - 1) < 0.02
+    finally:
+        pic.pic_destroy(h)
+        s.close()
