@@ -72,6 +72,7 @@ def _declare(L):
     L.orc_set_external_field.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.orc_work_function_field.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp]
     L.orc_set_particle_bc.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64]
+    L.orc_set_shape_order.argtypes = [C.c_void_p, C.c_int]
     L.orc_add_species.restype = C.c_int
     L.orc_add_species.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                                   _dp, C.c_double, C.c_long, _dp, _dp, _dp, C.c_int]
@@ -276,6 +277,10 @@ class OracleSim:
         out = [np.zeros(self.shape) for _ in range(3)]
         lib().orc_work_function_field(self._h, float(W_eV), *[a.ctypes.data_as(_dp) for a in out])
         return out
+
+    def set_shape_order(self, order):
+        """1 CIC, 2 TSC for the free and Dirac particles (before add_species)."""
+        lib().orc_set_shape_order(self._h, int(order))
 
     def set_particle_bc(self, open_edges=False, p_diffuse=0.0, seed=0):
         lib().orc_set_particle_bc(self._h, int(bool(open_edges)), float(p_diffuse), int(seed))

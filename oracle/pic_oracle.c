@@ -103,6 +103,9 @@ typedef struct {
     int open_edges;
     double p_diffuse;
     uint64_t diff_seed;
+    /* shape order of the free and Dirac particles: 1 CIC, 2 TSC (bound
+       particles are always CIC) */
+    int shape_order;
     double *rho_bg;
     long step;
     int nsp;
@@ -183,6 +186,7 @@ void *orc_create(int dims, const int *n, const double *d, double dt, const int *
     s->src_on = src_on; s->inc = inc; s->pol = pol; s->src_idx = src_idx;
     s->E0 = E0; s->omega = omega; s->tau = tau; s->t0 = t0;
     s->ncell = (long)s->n[0] * s->n[1] * s->n[2];
+    s->shape_order = 1;
     for (int c = 0; c < 3; ++c) {
         s->E[c] = (double *)calloc(s->ncell, sizeof(double));
         s->B[c] = (double *)calloc(s->ncell, sizeof(double));
@@ -322,17 +326,47 @@ static double cic(double X, int node) {
     return r < 1.0 ? 1.0 - r : 0.0;
 }
 
+/* TSC (quadratic B-spline, order 2) weight of the node at integer position
+   `node` for a particle at X: 3/4 - r^2 for r < 1/2, (3/2 - r)^2 / 2 for
+   1/2 <= r < 3/2, r = |X - node|. */
+static double tsc(double X, int node) {
+    double r = fabs(X - node);
+    if (r < 0.5) return 0.75 - r * r;
+    if (r < 1.5) {
+        double t = 1.5 - r;
+        return 0.5 * t * t;
+    }
+    return 0.0;
+}
+
+static double shape(int order, double X, int node) {
+    return order == 2 ? tsc(X, node) : cic(X, node);
+}
+
+/* first of the nodes a particle at X touches: CIC floor(X) (2 nodes), TSC
+   the nearest node - 1 (3 nodes) */
+static int first_node(int order, double X) {
+    return order == 2 ? (int)floor(X + 0.5) - 1 : (int)floor(X);
+}
+
+/* shape order of species sp (bound particles keep CIC) */
+static int species_order(const orc_sim *s, const orc_species *sp) {
+    return sp->kind == KIND_BOUND ? 1 : s->shape_order;
+}
+
 /* Deposit the charge density of one macro-particle (charge qw) at X onto the
-   integer nodes (Gauss-law nodes of the Yee grid). */
-static void deposit_rho(const orc_sim *s, double *rho, const double *X, double qw) {
+   integer nodes (Gauss-law nodes of the Yee grid) with the shape of the
+   given order. */
+static void deposit_rho(const orc_sim *s, int order, double *rho, const double *X, double qw) {
     double V = s->d[0] * s->d[1] * s->d[2];
-    int i0 = (int)floor(X[0]), j0 = (int)floor(X[1]), k0 = (int)floor(X[2]);
-    int kn = s->dims == 3 ? 2 : 1;
+    int nn = order + 1;
+    int i0 = first_node(order, X[0]), j0 = first_node(order, X[1]), k0 = first_node(order, X[2]);
+    int kn = s->dims == 3 ? nn : 1;
     for (int k = 0; k < kn; ++k)
-        for (int j = 0; j < 2; ++j)
-            for (int i = 0; i < 2; ++i) {
-                double wz = s->dims == 3 ? cic(X[2], k0 + k) : 1.0;
-                double w = cic(X[0], i0 + i) * cic(X[1], j0 + j) * wz;
+        for (int j = 0; j < nn; ++j)
+            for (int i = 0; i < nn; ++i) {
+                double wz = s->dims == 3 ? shape(order, X[2], k0 + k) : 1.0;
+                double w = shape(order, X[0], i0 + i) * shape(order, X[1], j0 + j) * wz;
                 fadd(s, rho, i0 + i, j0 + j, s->dims == 3 ? k0 + k : 0, qw / V * w);
             }
 }
@@ -354,7 +388,7 @@ void orc_rho(void *h, double *rho) {
         for (long p = 0; p < sp->n; ++p) {
             double X[3];
             particle_pos(s, sp, p, X);
-            deposit_rho(s, rho, X, sp->q * sp->w);
+            deposit_rho(s, species_order(s, sp), rho, X, sp->q * sp->w);
         }
     }
     if (s->rho_bg)
@@ -390,7 +424,8 @@ int orc_add_species(void *h, int kind, double q, double m, double w, const doubl
         if (!s->rho_bg) s->rho_bg = (double *)calloc(s->ncell, sizeof(double));
         if (bg_mode == 1) {
             /* ions at the loaded positions; for bound species at the anchors */
-            for (long p = 0; p < n; ++p) deposit_rho(s, s->rho_bg, &sp->X[3 * p], -q * w);
+            for (long p = 0; p < n; ++p)
+                deposit_rho(s, species_order(s, sp), s->rho_bg, &sp->X[3 * p], -q * w);
         } else {
             double V = s->d[0] * s->d[1] * s->d[2];
             double total = q * w * (double)n;
@@ -494,37 +529,48 @@ void orc_push_dirac(double *v, const double *E, const double *B, double q, doubl
 static const double STAG_E[3][3] = {{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
 static const double STAG_B[3][3] = {{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};
 
-static double interp(const orc_sim *s, const double *F, const double *stag, const double *X) {
+static double interp(const orc_sim *s, int order, const double *F, const double *stag,
+                     const double *X) {
     double u[3];
     int i0[3];
+    int nn = order + 1;
     for (int a = 0; a < 3; ++a) {
         u[a] = X[a] - stag[a];
-        i0[a] = (int)floor(u[a]);
+        i0[a] = first_node(order, u[a]);
     }
     double acc = 0.0;
-    int kn = s->dims == 3 ? 2 : 1;
+    int kn = s->dims == 3 ? nn : 1;
     for (int k = 0; k < kn; ++k)
-        for (int j = 0; j < 2; ++j)
-            for (int i = 0; i < 2; ++i) {
-                double wz = s->dims == 3 ? cic(u[2], i0[2] + k) : 1.0;
-                double w = cic(u[0], i0[0] + i) * cic(u[1], i0[1] + j) * wz;
+        for (int j = 0; j < nn; ++j)
+            for (int i = 0; i < nn; ++i) {
+                double wz = s->dims == 3 ? shape(order, u[2], i0[2] + k) : 1.0;
+                double w = shape(order, u[0], i0[0] + i) * shape(order, u[1], i0[1] + j) * wz;
                 acc += w * fget(s, F, i0[0] + i, i0[1] + j, s->dims == 3 ? i0[2] + k : 0);
             }
     return acc;
 }
 
-/* E^n and B^n at a particle (CIC on the Yee stagger, shape function W of
-   Sec. 4.1). */
-static void gather(const orc_sim *s, const double *X, double *E, double *B) {
+/* E^n and B^n at a particle on the Yee stagger with the shape function W
+   of Sec. 4.1 (CIC, or TSC for order 2). */
+static void gather(const orc_sim *s, int order, const double *X, double *E, double *B) {
     for (int c = 0; c < 3; ++c) {
-        E[c] = interp(s, s->E[c], STAG_E[c], X);
-        if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_E[c], X);
-        B[c] = interp(s, s->Bn[c], STAG_B[c], X);
+        E[c] = interp(s, order, s->E[c], STAG_E[c], X);
+        if (s->Eext[c]) E[c] += interp(s, order, s->Eext[c], STAG_E[c], X);
+        B[c] = interp(s, order, s->Bn[c], STAG_B[c], X);
     }
 }
 
+/* gather with the shape of the free particles (the simulation's order) */
 void orc_gather(void *h, const double *X, double *E, double *B) {
-    gather((const orc_sim *)h, X, E, B);
+    const orc_sim *s = (const orc_sim *)h;
+    gather(s, s->shape_order, X, E, B);
+}
+
+/* Shape order of the free and Dirac particles (1 CIC, 2 TSC); bound
+   particles stay CIC.  Call before orc_add_species (the ion background of a
+   species is deposited with its shape). */
+void orc_set_shape_order(void *h, int order) {
+    ((orc_sim *)h)->shape_order = order == 2 ? 2 : 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -536,48 +582,51 @@ void orc_gather(void *h, const double *X, double *E, double *B) {
    decomposition W; J_x(i+1/2) - J_x(i-1/2) = -(qw / (dy dz dt)) W_x(i), so
    J_x(i+1/2) is minus the running sum of W_x.  vz is the out-of-plane velocity
    used by the 2D3V form. */
-static void esirkepov(orc_sim *s, const double *X0, const double *X1, double qw, double vz) {
+static void esirkepov(orc_sim *s, int order, const double *X0, const double *X1, double qw,
+                      double vz) {
     const double dt = s->dt;
     const double *d = s->d;
+    /* nodes touched by the start and end shapes: CIC 3, TSC 4 per axis */
+    const int NS = order + 2;
     int lo[3];
-    double S0[3][3], DS[3][3];
+    double S0[3][4], DS[3][4];
     int na = s->dims;
     for (int a = 0; a < na; ++a) {
-        int c0 = (int)floor(X0[a]), c1 = (int)floor(X1[a]);
+        int c0 = first_node(order, X0[a]), c1 = first_node(order, X1[a]);
         lo[a] = c0 < c1 ? c0 : c1;
-        for (int m = 0; m < 3; ++m) {
-            S0[a][m] = cic(X0[a], lo[a] + m);
-            DS[a][m] = cic(X1[a], lo[a] + m) - S0[a][m];
+        for (int m = 0; m < NS; ++m) {
+            S0[a][m] = shape(order, X0[a], lo[a] + m);
+            DS[a][m] = shape(order, X1[a], lo[a] + m) - S0[a][m];
         }
     }
     if (s->dims == 3) {
         double fx = -qw / (d[1] * d[2] * dt);
         double fy = -qw / (d[0] * d[2] * dt);
         double fz = -qw / (d[0] * d[1] * dt);
-        for (int k = 0; k < 3; ++k)
-            for (int j = 0; j < 3; ++j) {
+        for (int k = 0; k < NS; ++k)
+            for (int j = 0; j < NS; ++j) {
                 double run = 0.0;
-                for (int i = 0; i < 3; ++i) {
+                for (int i = 0; i < NS; ++i) {
                     double W = DS[0][i] * (S0[1][j] * S0[2][k] + 0.5 * DS[1][j] * S0[2][k] +
                                            0.5 * S0[1][j] * DS[2][k] + DS[1][j] * DS[2][k] / 3.0);
                     run += W;
                     if (run != 0.0) fadd(s, s->J[0], lo[0] + i, lo[1] + j, lo[2] + k, fx * run);
                 }
             }
-        for (int k = 0; k < 3; ++k)
-            for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < NS; ++k)
+            for (int i = 0; i < NS; ++i) {
                 double run = 0.0;
-                for (int j = 0; j < 3; ++j) {
+                for (int j = 0; j < NS; ++j) {
                     double W = DS[1][j] * (S0[0][i] * S0[2][k] + 0.5 * DS[0][i] * S0[2][k] +
                                            0.5 * S0[0][i] * DS[2][k] + DS[0][i] * DS[2][k] / 3.0);
                     run += W;
                     if (run != 0.0) fadd(s, s->J[1], lo[0] + i, lo[1] + j, lo[2] + k, fy * run);
                 }
             }
-        for (int j = 0; j < 3; ++j)
-            for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < NS; ++j)
+            for (int i = 0; i < NS; ++i) {
                 double run = 0.0;
-                for (int k = 0; k < 3; ++k) {
+                for (int k = 0; k < NS; ++k) {
                     double W = DS[2][k] * (S0[0][i] * S0[1][j] + 0.5 * DS[0][i] * S0[1][j] +
                                            0.5 * S0[0][i] * DS[1][j] + DS[0][i] * DS[1][j] / 3.0);
                     run += W;
@@ -588,22 +637,22 @@ static void esirkepov(orc_sim *s, const double *X0, const double *X1, double qw,
         double fx = -qw / (d[1] * d[2] * dt);
         double fy = -qw / (d[0] * d[2] * dt);
         double fz = qw * vz / (d[0] * d[1] * d[2]);
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < NS; ++j) {
             double run = 0.0;
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < NS; ++i) {
                 run += DS[0][i] * (S0[1][j] + 0.5 * DS[1][j]);
                 if (run != 0.0) fadd(s, s->J[0], lo[0] + i, lo[1] + j, 0, fx * run);
             }
         }
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < NS; ++i) {
             double run = 0.0;
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < NS; ++j) {
                 run += DS[1][j] * (S0[0][i] + 0.5 * DS[0][i]);
                 if (run != 0.0) fadd(s, s->J[1], lo[0] + i, lo[1] + j, 0, fy * run);
             }
         }
-        for (int j = 0; j < 3; ++j)
-            for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < NS; ++j)
+            for (int i = 0; i < NS; ++i) {
                 double W = S0[0][i] * S0[1][j] + 0.5 * DS[0][i] * S0[1][j] +
                            0.5 * S0[0][i] * DS[1][j] + DS[0][i] * DS[1][j] / 3.0;
                 if (W != 0.0) fadd(s, s->J[2], lo[0] + i, lo[1] + j, 0, fz * W);
@@ -611,8 +660,10 @@ static void esirkepov(orc_sim *s, const double *X0, const double *X1, double qw,
     }
 }
 
+/* one deposit with the shape of the free particles */
 void orc_deposit_one(void *h, const double *X0, const double *X1, double qw, double vz) {
-    esirkepov((orc_sim *)h, X0, X1, qw, vz);
+    orc_sim *s = (orc_sim *)h;
+    esirkepov(s, s->shape_order, X0, X1, qw, vz);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -803,7 +854,8 @@ static void push_species(orc_sim *s, orc_species *sp, int k) {
         double X0[3], X1[3], E[3], B[3];
         double *v = &sp->V[3 * p];
         particle_pos(s, sp, p, X0);
-        gather(s, X0, E, B);
+        const int order = species_order(s, sp);
+        gather(s, order, X0, E, B);
         if (sp->kind == KIND_BOUND) {
             double *D = &sp->D[3 * p];
             orc_push_bound(v, D, E, B, sp->q, sp->m, dt, sp->omega0, sp->gamma);
@@ -814,7 +866,7 @@ static void push_species(orc_sim *s, orc_species *sp, int k) {
             for (int a = 0; a < 3; ++a) X1[a] = X0[a] + (a < s->dims ? dt * v[a] / s->d[a] : 0.0);
             sp->nrefl += reflect(s, sp, k, p, X0, X1, v);
         }
-        esirkepov(s, X0, X1, sp->q * sp->w, v[2]);
+        esirkepov(s, order, X0, X1, sp->q * sp->w, v[2]);
         if (sp->kind != KIND_BOUND) {
             for (int a = 0; a < s->dims; ++a) {
                 if (s->bc[a] == BC_PERIODIC) {

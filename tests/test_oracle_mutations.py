@@ -81,6 +81,11 @@ MUTATIONS = [
     ("2D law uniform in angle", "const double st = 2.0 * u1 - 1.0, ct = sqrt(1.0 - st * st);",
      "const double st = sin(PI * (u1 - 0.5)), ct = sqrt(1.0 - st * st);",
      "test_diffuse_reflection_of_dirac_carriers_is_2d_lambert"),
+    ("TSC central weight", "if (r < 0.5) return 0.75 - r * r;", "if (r < 0.5) return 0.7 - r * r;",
+     "test_tsc_weights_hand_computed or test_tsc_esirkepov_satisfies_continuity_exactly"),
+    ("TSC node window", "return order == 2 ? (int)floor(X + 0.5) - 1 : (int)floor(X);",
+     "return order == 2 ? (int)floor(X) - 1 : (int)floor(X);",
+     "test_tsc_weights_hand_computed or test_tsc_esirkepov_satisfies_continuity_exactly"),
     ("histogram edge", "if (E >= e_max) b = nbins;", "if (E > e_max) b = nbins;",
      "test_energy_histogram_bin_edges"),
     ("histogram energy factor", "double E = 0.5 * sp->m * ((v[0] * v[0]",

@@ -391,6 +391,99 @@ def test_esirkepov_satisfies_continuity_exactly():
             s.close()
 
 
+def _rho_tsc(dims, n, X, qv):
+    """Brute force: TSC weights of every node (periodic) for a point charge;
+    the quadratic B-spline is 3/4 - d^2 below 1/2, (3/2 - d)^2 / 2 below 3/2."""
+    nx, ny, nz = n
+    out = np.zeros((nz, ny, nx))
+    for k in range(nz if dims == 3 else 1):
+        for j in range(ny):
+            for i in range(nx):
+                w = 1.0
+                for a, idx in enumerate((i, j, k)[:dims]):
+                    L = n[a]
+                    d = (X[a] - idx) % L
+                    d = min(d, L - d)
+                    w *= 0.75 - d * d if d < 0.5 else (0.5 * (1.5 - d) ** 2 if d < 1.5 else 0.0)
+                out[k, j, i] = qv * w
+    return out
+
+
+def test_tsc_weights_hand_computed():
+    """A unit E_x at the single node (3.5, 3, 3) gathered at (3.8, 3.3,
+    2.6) with TSC: offsets 0.3, 0.3, -0.4 give 0.66 x 0.66 x 0.59; the
+    nodes one further out give (3/2 - 1.3)^2 / 2 = 0.02 along x."""
+    s = O.OracleSim(**_grid3(bc=(0, 0, 0)))
+    s.set_shape_order(2)
+    Ex = np.zeros(s.shape)
+    Ex[3, 3, 3] = 1.0
+    s.set_field(0, Ex)
+    E, _ = s.gather(np.array([3.8, 3.3, 2.6]))
+    assert E[0] == pytest.approx(0.66 * 0.66 * 0.59, rel=1e-13)
+    E, _ = s.gather(np.array([4.8, 3.3, 2.6]))  # x offset 1.3 from the node
+    assert E[0] == pytest.approx(0.02 * 0.66 * 0.59, rel=1e-12)
+    E, _ = s.gather(np.array([5.1, 3.3, 2.6]))  # 1.6: beyond the support
+    assert E[0] == 0.0
+
+
+def test_tsc_gather_is_exact_for_linear_fields():
+    """TSC, like CIC, reproduces fields linear in position when the nodes
+    sit at the Yee stagger."""
+    s = O.OracleSim(**_grid3(bc=(1, 1, 1), pml_cells=0))
+    s.set_shape_order(2)
+    nz, ny, nx = s.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    stagE = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5)]
+    coef = np.array([[1.0, 2.0, -3.0, 0.5], [2.0, -1.0, 0.25, 1.5], [-1.0, 0.5, 1.0, -2.0]])
+    for c in range(3):
+        a = coef[c]
+        sx, sy, sz = stagE[c]
+        s.set_field(c, a[0] + a[1] * (i + sx) + a[2] * (j + sy) + a[3] * (k + sz))
+    for _ in range(20):
+        X = RNG.uniform([2.1, 2.1, 2.1], [5.0, 4.0, 3.0])
+        E, _ = s.gather(X)
+        for c in range(3):
+            a = coef[c]
+            assert abs(E[c] - (a[0] + a[1] * X[0] + a[2] * X[1] + a[3] * X[2])) < 1e-12
+
+
+def test_tsc_esirkepov_satisfies_continuity_exactly():
+    """With TSC shapes: (rho(X1) - rho(X0))/dt + div J = 0 at every node
+    against brute-force TSC charge densities, for moves with and without
+    crossings of the nearest node, in 3D and 2D3V, across periodic edges;
+    total current = charge x velocity."""
+    for dims in (3, 2):
+        n = (7, 6, 5) if dims == 3 else (7, 6, 1)
+        g = dict(dims=dims, n=n, d=(1e-9, 1.3e-9, 0.8e-9), dt=1e-17, bc=(0, 0, 0))
+        for trial in range(20):
+            s = O.OracleSim(**g)
+            s.set_shape_order(2)
+            X0 = RNG.uniform(0, 1, 3) * np.array(n)
+            dX = RNG.uniform(-0.9, 0.9, 3)
+            if trial % 3 == 0:
+                dX *= 0.05
+            if dims == 2:
+                dX[2] = 0
+            X1 = X0 + dX
+            qw = -QE * 1e3
+            s.deposit_one(X0, X1, qw, vz=2e5)
+            Jx, Jy, Jz = s.J(0), s.J(1), s.J(2)
+            V = 1e-9 * 1.3e-9 * 0.8e-9
+            r0 = _rho_tsc(dims, n, X0, qw / V)
+            r1 = _rho_tsc(dims, n, X1, qw / V)
+            div = (Jx - np.roll(Jx, 1, axis=2)) / 1e-9 + (Jy - np.roll(Jy, 1, axis=1)) / 1.3e-9
+            if dims == 3:
+                div += (Jz - np.roll(Jz, 1, axis=0)) / 0.8e-9
+            res = (r1 - r0) / 1e-17 + div
+            assert np.abs(res).max() < 1e-12 * np.abs(r0).max() / 1e-17
+            vel = dX * np.array([1e-9, 1.3e-9, 0.8e-9]) / 1e-17
+            assert abs(Jx.sum() * V - qw * vel[0]) < 1e-12 * abs(qw) * 1e8 + 1e-12 * abs(qw * vel[0])
+            assert abs(Jy.sum() * V - qw * vel[1]) < 1e-12 * abs(qw) * 1e8 + 1e-12 * abs(qw * vel[1])
+            if dims == 2:
+                assert abs(Jz.sum() * V - qw * 2e5) < 1e-12 * abs(qw * 2e5)
+            s.close()
+
+
 def _rho_cic(dims, n, X, qv):
     """Brute force: CIC weights of every node (periodic) for a point charge."""
     nx, ny, nz = n
@@ -476,10 +569,11 @@ def test_reflection_hand_computed():
         assert nr == int(v[12])
 
 
-def _sphere_setup(seed=5, n=12, with_bound=True, bg=1, bc=(1, 1, 1)):
+def _sphere_setup(seed=5, n=12, with_bound=True, bg=1, bc=(1, 1, 1), order=1):
     g = dict(dims=3, n=(n, n, n), d=(0.5e-9,) * 3, dt=0.5 * 0.5e-9 / (C * math.sqrt(3)),
              bc=bc, pml_cells=2 if bc[0] else 0)
     s = O.OracleSim(**g)
+    s.set_shape_order(order)
     kk, jj, ii = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
     r = np.sqrt((ii + 0.5 - n / 2) ** 2 + (jj + 0.5 - n / 2) ** 2 + (kk + 0.5 - n / 2) ** 2)
     mask = (r < n / 2 - 2.5).astype(np.uint8)
@@ -517,11 +611,13 @@ def test_reflection_conserves_count_and_keeps_particles_inside():
     assert np.array_equal(s.cell_counts(0).sum(), n0)
 
 
-def test_gauss_law_is_preserved_by_the_step():
+@pytest.mark.parametrize("order", [1, 2])
+def test_gauss_law_is_preserved_by_the_step(order):
     """Charge-conserving deposit + Yee: div E - rho/eps0 stays at its initial
     value (zero here: quiet ions at the loaded positions, E = 0).  Periodic
-    walls: the CPML layer is not a charge-conserving medium."""
-    s, _ = _sphere_setup(with_bound=True, bg=1, bc=(0, 0, 0))
+    walls: the CPML layer is not a charge-conserving medium.  Order 2: the
+    free electrons deposit and gather with TSC, the bound ones with CIC."""
+    s, _ = _sphere_setup(with_bound=True, bg=1, bc=(0, 0, 0), order=order)
     d0 = s.diag()
     qscale = QE * 5.9e28 / 8 / EPS0  # charge density of one macro-particle / eps0
     assert d0["gauss_max"] < 1e-12 * qscale
