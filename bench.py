@@ -65,6 +65,8 @@ def parse():
                          "reflection, open edges, or open edges + work-function barrier")
     ap.add_argument("--diffuse-p", type=float, default=0.5, help="diffuse share, --surface diffuse")
     ap.add_argument("--work-function", type=float, default=5.1, help="eV, --surface wall")
+    ap.add_argument("--shape-order", type=int, default=1, choices=[1, 2],
+                    help="shape of the free particles: 1 CIC, 2 TSC (bound stay CIC)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
     ap.add_argument("--no-graphene", action="store_true", help="skip the graphene-sheet leg")
@@ -230,9 +232,9 @@ def traffic_from_profile(kernel_name, src_files):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def build_sim(pic, I, wl, stream, tuning=None):
+def build_sim(pic, I, wl, stream, tuning=None, shape_order=1):
     from paper_2501_07465_gb300 import runner
-    return runner.make_sim(wl, stream, tuning)
+    return runner.make_sim(wl, stream, tuning, shape_order)
 
 
 def apply_surface(pic, h, args):
@@ -282,7 +284,7 @@ def run_gpu(args):
         tuning["field_zchunk"] = args.zchunk
     tuning["field_mode"] = args.field_mode
     split = args.field_mode == 2
-    h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning)
+    h = build_sim(pic, I, wl, stream.cuda_stream, tuning=tuning, shape_order=args.shape_order)
     apply_surface(pic, h, args)
     diag0 = pic.pic_diagnostics(h)
     nparts = sum(diag0["count"])
@@ -381,6 +383,7 @@ def run_gpu(args):
                    "field_mode": {1: "fused (shared memory)", 2: "split B/E passes",
                                   3: "one streaming pass"}[args.field_mode],
                    "surface": surface_config(args),
+                   "shape": {1: "CIC", 2: "TSC (free), CIC (bound)"}[args.shape_order],
                    "l2": "inputs larger than L2 (fields 805 MB, no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "kernel": kd["name"], "achieved": achieved,

@@ -270,6 +270,17 @@ pic_status pic_set_work_function(pic_sim *sim, double W_eV);
    with p_diffuse > 0 steps alone (pic_group_add refuses it). */
 pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64_t seed);
 
+/* Shape function W of Sec. 4.1 for the free and Dirac particles: order 1
+   CIC (default), 2 TSC (the quadratic B-spline: 3/4 - r^2 for r < 1/2,
+   (3/2 - r)^2 / 2 for r < 3/2; gather from the three nodes around the
+   nearest one on each component's stagger, Esirkepov deposit over four
+   nodes per axis, and the charge density of the Gauss diagnostic with the
+   same shape).  Bound particles keep CIC.  Must precede pic_load_species
+   (PIC_ESTATE otherwise: a species' ion background is deposited with its
+   shape); other orders: PIC_EINVAL.  A TSC simulation steps alone
+   (pic_group_add refuses it). */
+pic_status pic_set_shape_order(pic_sim *sim, int order);
+
 /* Add a species (explicit particles or the Fermi-Dirac loader) and sort it
    into tiles.  Re-checks Eq. dtlimit with the plasma and binding frequencies
    of all species so far (PIC_EDTLIMIT).  *species_id receives its index. */

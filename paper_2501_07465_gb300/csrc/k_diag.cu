@@ -116,8 +116,17 @@ __device__ inline int wrap_or_neg(int i, int n, int per) {
     return r < 0 ? r + n : r;
 }
 
-// CIC charge density on the integer nodes, FP64 atomics.
-__global__ void rho_kernel(GridP g, SpeciesP sp, double qv, double *rho) {
+// TSC weight of a node at distance r (order 2, the quadratic B-spline).
+__device__ inline double tsc_w(double r) {
+    r = fabs(r);
+    if (r < 0.5) return 0.75 - r * r;
+    if (r < 1.5) return 0.5 * (1.5 - r) * (1.5 - r);
+    return 0.0;
+}
+
+// Charge density on the integer nodes with the species' shape (CIC, or TSC
+// for order 2: the three nodes around the nearest), FP64 atomics.
+__global__ void rho_kernel(GridP g, SpeciesP sp, double qv, int order, double *rho) {
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < sp.n;
          p += (long long)gridDim.x * blockDim.x) {
         uint32_t c = sp.cell[p];
@@ -128,6 +137,23 @@ __global__ void rho_kernel(GridP g, SpeciesP sp, double qv, double *rho) {
                 X[a] = ci[a] + sp.anchor[a][p] + (double)sp.disp[a][p] * (double)g.inv_d[a];
             else
                 X[a] = ci[a] + (double)sp.o[a][p];
+        }
+        if (order == 2) {
+            int n0[3];
+            for (int a = 0; a < 3; ++a) n0[a] = (int)floor(X[a] + 0.5) - 1;
+            const int kn = g.dims == 3 ? 3 : 1;
+            for (int k = 0; k < kn; ++k)
+                for (int j = 0; j < 3; ++j)
+                    for (int i = 0; i < 3; ++i) {
+                        double w = tsc_w(X[0] - (n0[0] + i)) * tsc_w(X[1] - (n0[1] + j));
+                        if (g.dims == 3) w *= tsc_w(X[2] - (n0[2] + k));
+                        int gx = wrap_or_neg(n0[0] + i, g.n[0], g.per[0]);
+                        int gy = wrap_or_neg(n0[1] + j, g.n[1], g.per[1]);
+                        int gz = g.dims == 3 ? wrap_or_neg(n0[2] + k, g.n[2], g.per[2]) : 0;
+                        if (gx < 0 || gy < 0 || gz < 0) continue;
+                        atomicAdd(&rho[((long long)gz * g.n[1] + gy) * g.n[0] + gx], qv * w);
+                    }
+            continue;
         }
         int i0 = (int)floor(X[0]), j0 = (int)floor(X[1]), k0 = (int)floor(X[2]);
         double fx = X[0] - i0, fy = X[1] - j0, fz = X[2] - k0;
@@ -270,10 +296,10 @@ cudaError_t launch_field_energy(const GridP &g, const float *const *E, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V, double *rho,
-                               cudaStream_t s) {
+cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V, int order,
+                               double *rho, cudaStream_t s) {
     if (sp.n <= 0) return cudaSuccess;
-    rho_kernel<<<blocks_for(sp.n), 256, 0, s>>>(g, sp, qw_over_V, rho);
+    rho_kernel<<<blocks_for(sp.n), 256, 0, s>>>(g, sp, qw_over_V, order, rho);
     return cudaGetLastError();
 }
 

@@ -45,11 +45,15 @@ cudaError_t particle_setup_dim(size_t smem, int *ctas_per_sm) {
                                                          kThreads, smem);
 }
 
-cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext) {
+cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext,
+                                  int *ctas_per_sm_tsc) {
     cudaError_t e = dims == 3 ? particle_setup_dim<3>(smem, ctas_per_sm)
                               : particle_setup_dim<2>(smem, ctas_per_sm);
-    if (e != cudaSuccess || !ctas_per_sm_ext) return e;
-    return particle_ext_setup(dims, smem, ctas_per_sm_ext);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm_ext && (e = particle_ext_setup(dims, smem, ctas_per_sm_ext)) != cudaSuccess)
+        return e;
+    if (ctas_per_sm_tsc) return particle_tsc_setup(dims, smem, ctas_per_sm_tsc);
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
@@ -67,6 +71,7 @@ cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const 
 
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s) {
     if (nctas < 1) nctas = 1;
+    if (pl.shape == 2) return launch_particles_tsc(pl, nctas, smem, s);
     if (particle_launch_ext(pl)) return launch_particles_ext(pl, nctas, smem, s);
     if (pl.g.dims == 3) particle_kernel<3><<<nctas, kThreads, smem, s>>>(pl);
     else particle_kernel<2><<<nctas, kThreads, smem, s>>>(pl);

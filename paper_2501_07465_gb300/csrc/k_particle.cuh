@@ -1,7 +1,8 @@
 // k_particle.cuh -- device code of the particle phase (see k_particle.cu),
-// shared by the two translation units that instantiate it: k_particle.cu
-// (the plain kernels and the batch kernel) and k_particle_ext.cu (the
-// kernels with the boundary variants of Sec. 3), compiled in parallel.
+// shared by the translation units that instantiate it: k_particle.cu (the
+// plain kernels and the batch kernel), k_particle_ext.cu (the kernels with
+// the boundary variants of Sec. 3) and k_particle_tsc.cu (TSC shapes for
+// the free and Dirac particles), compiled in parallel.
 #pragma once
 
 #include "pic_internal.cuh"
@@ -31,20 +32,24 @@ __device__ inline int wrap_or_neg(int i, int n, int per) {
 // Components: 0..2 E, 3..5 B^n.  Coordinates are "local" integers: box
 // coordinates (local cell + 2) for the box, global cell indices (possibly
 // outside [0,n)) for the global accessor.
-struct BoxAcc {
+// H: halo of the box in cells (2; 3 for the TSC kernel, whose three-node
+// gather and four-node deposit reach one node further)
+template <int H>
+struct BoxAccT {
     float *F[6];
     float *J[3];
     int b0, b01;
-    int hz;  // halo along z: 2 in 3D, 0 in 2D
+    int hz;  // halo along z: H in 3D, 0 in 2D
     // local cell coordinates (relative to the tile origin) -> box index
     __device__ inline int idx(int x, int y, int z) const {
-        return (z + hz) * b01 + (y + kHalo) * b0 + (x + kHalo);
+        return (z + hz) * b01 + (y + H) * b0 + (x + H);
     }
     __device__ inline float get(int c, int x, int y, int z) const { return F[c][idx(x, y, z)]; }
     __device__ inline void add(int c, int x, int y, int z, float v) const {
         atomicAdd(&J[c][idx(x, y, z)], v);
     }
 };
+using BoxAcc = BoxAccT<kHalo>;
 
 template <int DIM, bool X>
 struct GlobalAcc {
@@ -165,6 +170,191 @@ __device__ inline void gather(const Acc &A, const int *l, const float *f, float 
     B[2] = interp<DIM>(A, 5, w, true, true, false);
 }
 
+// ---------------------------------------------------------------------------
+// TSC (order 2) gather: three nodes per axis around the nearest one
+// ---------------------------------------------------------------------------
+
+// First node n and the three weights for an offset x in [-1/2, 1/2) from
+// the nearest node n + 1: (1/2 - x)^2 / 2, 3/4 - x^2, (1/2 + x)^2 / 2.
+struct AxisT {
+    int n;
+    float w[3];
+};
+
+__device__ inline AxisT tsc_axis(int nearest, float x) {
+    AxisT a;
+    a.n = nearest - 1;
+    const float l = 0.5f - x, r = 0.5f + x;
+    a.w[0] = 0.5f * l * l;
+    a.w[1] = 0.75f - x * x;
+    a.w[2] = 0.5f * r * r;
+    return a;
+}
+
+// integer-staggered nodes: nearest of l + f; half-staggered (at m + 1/2): m = l
+__device__ inline AxisT tsc_int(int l, float f) {
+    return f >= 0.5f ? tsc_axis(l + 1, f - 1.f) : tsc_axis(l, f);
+}
+__device__ inline AxisT tsc_half(int l, float f) { return tsc_axis(l, f - 0.5f); }
+
+template <int DIM, class Acc>
+__device__ inline float interp_tsc(const Acc &A, int c, const AxisT &ax, const AxisT &ay,
+                                   const AxisT &az) {
+    float acc = 0.f;
+    const int kn = DIM == 3 ? 3 : 1;
+#pragma unroll
+    for (int k = 0; k < kn; ++k) {
+        float pl = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int z = DIM == 3 ? az.n + k : 0;
+            const float row = ax.w[0] * A.get(c, ax.n, ay.n + j, z) +
+                              ax.w[1] * A.get(c, ax.n + 1, ay.n + j, z) +
+                              ax.w[2] * A.get(c, ax.n + 2, ay.n + j, z);
+            pl += ay.w[j] * row;
+        }
+        acc += DIM == 3 ? az.w[k] * pl : pl;
+    }
+    return acc;
+}
+
+// E^n, B^n at a particle with TSC weights on each component's stagger.
+template <int DIM, class Acc>
+__device__ inline void gather_tsc(const Acc &A, const int *l, const float *f, float *E,
+                                  float *B) {
+    const AxisT ix = tsc_int(l[0], f[0]), hx = tsc_half(l[0], f[0]);
+    const AxisT iy = tsc_int(l[1], f[1]), hy = tsc_half(l[1], f[1]);
+    const AxisT iz = DIM == 3 ? tsc_int(l[2], f[2]) : ix;
+    const AxisT hz = DIM == 3 ? tsc_half(l[2], f[2]) : ix;
+    E[0] = interp_tsc<DIM>(A, 0, hx, iy, iz);
+    E[1] = interp_tsc<DIM>(A, 1, ix, hy, iz);
+    E[2] = interp_tsc<DIM>(A, 2, ix, iy, hz);
+    B[0] = interp_tsc<DIM>(A, 3, ix, hy, hz);
+    B[1] = interp_tsc<DIM>(A, 4, hx, iy, hz);
+    B[2] = interp_tsc<DIM>(A, 5, hx, hy, iz);
+}
+
+// Change of the three TSC weights around one nearest node for a move from
+// offset x by d (x and x + d within [-1/2, 1/2]), without cancellation:
+// -d (1/2 - x - d/2), -d (2x + d), d (1/2 + x + d/2) (they sum to zero).
+__device__ inline void tsc_delta(float x, float d, float *o) {
+    o[0] = -d * (0.5f - x - 0.5f * d);
+    o[1] = -d * (2.f * x + d);
+    o[2] = d * (0.5f + x + 0.5f * d);
+}
+
+// Esirkepov deposit with TSC shapes for a move from cell c0 + offset f0 to
+// cell c1 + offset f1 (less than one cell per axis): on each axis the start
+// and end shapes live on the four nodes lo .. lo + 3, lo = min(nearest) - 1;
+// the weight changes DS are formed from the displacement (a move that
+// changes the nearest node is split at the half-integer point between the
+// two), so a small move keeps its relative precision in FP32.  W as in the
+// CIC deposit, and J_a at face i + 1/2 is the running sum of W_a along a up
+// to node i (the flux through the last face is zero).
+template <int DIM, class Acc>
+__device__ inline void deposit_tsc(const Acc &A, const int *c0, const float *f0, const int *c1,
+                                   const float *f1, const float *jfac, float vz) {
+    int lo[3] = {0, 0, 0};
+    float S0[3][4] = {}, DS[3][4] = {};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const bool u0 = f0[a] >= 0.5f, u1 = f1[a] >= 0.5f;
+        const int n0 = c0[a] + (u0 ? 1 : 0), n1 = c1[a] + (u1 ? 1 : 0);
+        const float x0 = u0 ? f0[a] - 1.f : f0[a];
+        const float x1 = u1 ? f1[a] - 1.f : f1[a];
+        const AxisT t0 = tsc_axis(n0, x0);
+        float da[3], db[3];
+        if (n1 == n0) {
+            lo[a] = n0 - 1;
+            tsc_delta(x0, x1 - x0, da);
+            S0[a][0] = t0.w[0]; S0[a][1] = t0.w[1]; S0[a][2] = t0.w[2]; S0[a][3] = 0.f;
+            DS[a][0] = da[0]; DS[a][1] = da[1]; DS[a][2] = da[2]; DS[a][3] = 0.f;
+        } else if (n1 > n0) {
+            // up to the point n0 + 1/2, then on around n0 + 1
+            lo[a] = n0 - 1;
+            tsc_delta(x0, 0.5f - x0, da);
+            tsc_delta(-0.5f, x1 + 0.5f, db);
+            S0[a][0] = t0.w[0]; S0[a][1] = t0.w[1]; S0[a][2] = t0.w[2]; S0[a][3] = 0.f;
+            DS[a][0] = da[0]; DS[a][1] = da[1] + db[0]; DS[a][2] = da[2] + db[1];
+            DS[a][3] = db[2];
+        } else {
+            // down to the point n0 - 1/2, then on around n0 - 1
+            lo[a] = n0 - 2;
+            tsc_delta(x0, -0.5f - x0, da);
+            tsc_delta(0.5f, x1 - 0.5f, db);
+            S0[a][0] = 0.f; S0[a][1] = t0.w[0]; S0[a][2] = t0.w[1]; S0[a][3] = t0.w[2];
+            DS[a][0] = db[0]; DS[a][1] = db[1] + da[0]; DS[a][2] = db[2] + da[1];
+            DS[a][3] = da[2];
+        }
+    }
+    const float third = 1.0f / 3.0f;
+    if (DIM == 3) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float run = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    run += DS[0][i] * (S0[1][j] * S0[2][k] + 0.5f * DS[1][j] * S0[2][k] +
+                                       0.5f * S0[1][j] * DS[2][k] + DS[1][j] * DS[2][k] * third);
+                    if (run != 0.f) A.add(0, lo[0] + i, lo[1] + j, lo[2] + k, jfac[0] * run);
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float run = 0.f;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    run += DS[1][j] * (S0[0][i] * S0[2][k] + 0.5f * DS[0][i] * S0[2][k] +
+                                       0.5f * S0[0][i] * DS[2][k] + DS[0][i] * DS[2][k] * third);
+                    if (run != 0.f) A.add(1, lo[0] + i, lo[1] + j, lo[2] + k, jfac[1] * run);
+                }
+            }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float run = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    run += DS[2][k] * (S0[0][i] * S0[1][j] + 0.5f * DS[0][i] * S0[1][j] +
+                                       0.5f * S0[0][i] * DS[1][j] + DS[0][i] * DS[1][j] * third);
+                    if (run != 0.f) A.add(2, lo[0] + i, lo[1] + j, lo[2] + k, jfac[2] * run);
+                }
+            }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float run = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                run += DS[0][i] * (S0[1][j] + 0.5f * DS[1][j]);
+                if (run != 0.f) A.add(0, lo[0] + i, lo[1] + j, 0, jfac[0] * run);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float run = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                run += DS[1][j] * (S0[0][i] + 0.5f * DS[0][i]);
+                if (run != 0.f) A.add(1, lo[0] + i, lo[1] + j, 0, jfac[1] * run);
+            }
+        }
+        const float fz = jfac[2] * vz;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float W = S0[0][i] * S0[1][j] + 0.5f * DS[0][i] * S0[1][j] +
+                                0.5f * S0[0][i] * DS[1][j] + DS[0][i] * DS[1][j] * third;
+                if (W != 0.f) A.add(2, lo[0] + i, lo[1] + j, 0, fz * W);
+            }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Esirkepov deposit (order 1)
@@ -468,6 +658,9 @@ __device__ inline void local_cell(const ParticleLaunch &P, const int *gc, const 
     }
 }
 
+// The staged box serves a particle in local cell c in [-1, T]: CIC with the
+// box of local cells -2 .. T+2; TSC (its three-node gather and four-node
+// deposit reach one node further) with the box of cells -3 .. T+3.
 template <int DIM>
 __device__ inline bool in_core(const ParticleLaunch &P, const int *c) {
     bool ok = true;
@@ -505,10 +698,10 @@ __device__ inline void diffuse_velocity(float *v, int ax, int sgn, float u1, flo
     }
 }
 
-// Free electrons and Dirac carriers (species index si).
-template <int DIM, int KIND, bool X>
+// Free electrons and Dirac carriers (species index si), shape order S.
+template <int DIM, int KIND, bool X, int S = 1, class Box = BoxAcc>
 __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &s, int si,
-                                       long long p, const int *org, const BoxAcc &box,
+                                       long long p, const int *org, const Box &box,
                                        const GlobalAcc<DIM, X> &glob) {
     const GridP &g = P.g;
     const uint32_t pc = s.cell[p];
@@ -519,8 +712,13 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
     float f0[3] = {s.o[0][p], s.o[1][p], DIM == 3 ? s.o[2][p] : 0.f};
     float E[3], B[3];
     const bool fast = in_core<DIM>(P, lc);
-    if (fast) gather<DIM>(box, lc, f0, E, B);
-    else gather<DIM>(glob, gc, f0, E, B);
+    if constexpr (S == 2) {
+        if (fast) gather_tsc<DIM>(box, lc, f0, E, B);
+        else gather_tsc<DIM>(glob, gc, f0, E, B);
+    } else {
+        if (fast) gather<DIM>(box, lc, f0, E, B);
+        else gather<DIM>(glob, gc, f0, E, B);
+    }
 
     if (KIND == PIC_DIRAC) dirac_push(v, E, B, s);
     else boris(v, E, B, s.hq);
@@ -571,7 +769,22 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
             refl = 1;
         }
     }
-    if (!(sh[0] | sh[1] | sh[2])) {
+    if constexpr (S == 2) {
+        const int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
+        if (fast) deposit_tsc<DIM>(box, lc, f0, c1l, f1, s.jfac, v[2]);
+        else {
+            const int g1[3] = {gc[0] + sh[0], gc[1] + sh[1], gc[2] + sh[2]};
+            deposit_tsc<DIM>(glob, gc, f0, g1, f1, s.jfac, v[2]);
+        }
+        if (sh[0] | sh[1] | sh[2]) {
+            int nxc[3];
+            for (int a = 0; a < 3; ++a) {
+                nxc[a] = gc[a] + sh[a];
+                if (a < DIM && g.per[a]) nxc[a] = wrap_or_neg(nxc[a], g.n[a], 1);
+            }
+            s.cell[p] = pack_cell(nxc[0], nxc[1], nxc[2]);
+        }
+    } else if (!(sh[0] | sh[1] | sh[2])) {
         // stays in its cell: f1 - f0 is exact in FP32 (Sterbenz)
         const float dF[3] = {f1[0] - f0[0], f1[1] - f0[1], DIM == 3 ? f1[2] - f0[2] : 0.f};
         if (fast) deposit_nocross<DIM>(box, lc, f0, dF, s.jfac, v[2]);
@@ -605,9 +818,9 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
 // directly: it is far below an FP32 ulp of the offset, and the displacement D
 // itself is ~100x the per-step move, so differences of stored values would
 // lose most of its bits.
-template <int DIM, bool X>
+template <int DIM, bool X, class Box = BoxAcc>
 __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, long long p,
-                                  const int *org, const BoxAcc &box,
+                                  const int *org, const Box &box,
                                   const GlobalAcc<DIM, X> &glob) {
     const GridP &g = P.g;
     const uint32_t pc = s.cell[p];
@@ -621,10 +834,10 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, lo
     float f0[3] = {0.f, 0.f, 0.f}, f1[3] = {0.f, 0.f, 0.f};
     for (int a = 0; a < DIM; ++a) {
         an[a] = s.anchor32[a][p];
-        float X = an[a] + D[a] * g.inv_d[a];
-        float fl = floorf(X);
+        float xa = an[a] + D[a] * g.inv_d[a];
+        float fl = floorf(xa);
         c0[a] = lc[a] + (int)fl;
-        f0[a] = clamp_below_one(X - fl);
+        f0[a] = clamp_below_one(xa - fl);
     }
     float E[3], B[3];
     const bool fast = in_core<DIM>(P, c0);
@@ -723,17 +936,18 @@ struct BoxWalk {
 // the tile (all species), flush the J box.  P must live in parameter or shared
 // memory (not global), so that the compiler keeps its fields in registers
 // across the particle stores.
-template <int DIM, bool X>
+template <int DIM, bool X, int S = 1>
 __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, unsigned *s_refl) {
+    constexpr int H = S == 2 ? 3 : kHalo;  // box halo (cells)
     const TileP &tp = P.tp;
     const int bn = tp.boxn;
     const int B0 = tp.box[0], B1 = tp.box[1];
-    BoxAcc box;
+    BoxAccT<H> box;
     for (int c = 0; c < 6; ++c) box.F[c] = smem + c * bn;
     for (int c = 0; c < 3; ++c) box.J[c] = smem + (6 + c) * bn;
     box.b0 = B0;
     box.b01 = B0 * B1;
-    box.hz = DIM == 3 ? kHalo : 0;
+    box.hz = DIM == 3 ? H : 0;
     GlobalAcc<DIM, X> glob;
     glob.g = &P.g;
     glob.E = P.E;
@@ -754,9 +968,9 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
     {
         BoxWalk w;
         for (w.start(B0, B1, threadIdx.x, step); w.e < bn; w.next(B0, B1, step)) {
-            int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+            int gx = wrap_or_neg(org[0] + w.bx - H, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + w.by - H, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - H, g.n[2], g.per[2]) : 0;
             bool in = gx >= 0 && gy >= 0 && gz >= 0;
             long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
 #pragma unroll
@@ -776,9 +990,9 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
             const bool hx = w.bx + 1 < B0, hy = w.by + 1 < B1;
             const bool hz = DIM == 2 || w.bz + 1 < tp.box[2];
             if (!(hx && hy && hz)) continue;  // never gathered
-            int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+            int gx = wrap_or_neg(org[0] + w.bx - H, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + w.by - H, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - H, g.n[2], g.per[2]) : 0;
             if (gx < 0 || gy < 0 || gz < 0) {
                 box.F[3][e] = box.F[4][e] = box.F[5][e] = 0.f;
                 continue;
@@ -804,9 +1018,9 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
         // takes the curl of the Maxwell E alone
         BoxWalk w;
         for (w.start(B0, B1, threadIdx.x, step); w.e < bn; w.next(B0, B1, step)) {
-            int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
-            int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
-            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+            int gx = wrap_or_neg(org[0] + w.bx - H, g.n[0], g.per[0]);
+            int gy = wrap_or_neg(org[1] + w.by - H, g.n[1], g.per[1]);
+            int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - H, g.n[2], g.per[2]) : 0;
             if (gx < 0 || gy < 0 || gz < 0) continue;
             const long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
 #pragma unroll
@@ -823,10 +1037,10 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
                 push_bound<DIM, X>(P, s, p, org, box, glob);
         } else if (s.kind == PIC_DIRAC) {
             for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                r += push_mobile<DIM, PIC_DIRAC, X>(P, s, si, p, org, box, glob);
+                r += push_mobile<DIM, PIC_DIRAC, X, S>(P, s, si, p, org, box, glob);
         } else {
             for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                r += push_mobile<DIM, PIC_FREE, X>(P, s, si, p, org, box, glob);
+                r += push_mobile<DIM, PIC_FREE, X, S>(P, s, si, p, org, box, glob);
         }
         if (r) atomicAdd(&s_refl[si], r);
     }
@@ -842,9 +1056,9 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
             const int e = w.e;
             const float jx = box.J[0][e], jy = box.J[1][e], jz = box.J[2][e];
             if (jx != 0.f || jy != 0.f || jz != 0.f) {
-                int gx = wrap_or_neg(org[0] + w.bx - kHalo, g.n[0], g.per[0]);
-                int gy = wrap_or_neg(org[1] + w.by - kHalo, g.n[1], g.per[1]);
-                int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - kHalo, g.n[2], g.per[2]) : 0;
+                int gx = wrap_or_neg(org[0] + w.bx - H, g.n[0], g.per[0]);
+                int gy = wrap_or_neg(org[1] + w.by - H, g.n[1], g.per[1]);
+                int gz = DIM == 3 ? wrap_or_neg(org[2] + w.bz - H, g.n[2], g.per[2]) : 0;
                 if (gx >= 0 && gy >= 0 && gz >= 0) {
                     const long long o = ((long long)gz * g.n[1] + gy) * g.n[0] + gx;
                     if (jx != 0.f) atomicAdd(P.J[0] + o, jx);
@@ -861,7 +1075,7 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
 }
 
 // One particle phase: the persistent CTAs take tiles from the active list.
-template <int DIM, bool X>
+template <int DIM, bool X, int S = 1>
 __device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
@@ -877,7 +1091,7 @@ __device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
         __syncthreads();
         const int it = s_next;
         if (it >= nact) break;
-        tile_pass<DIM, X>(P, P.active[it], smem, s_refl);
+        tile_pass<DIM, X, S>(P, P.active[it], smem, s_refl);
     }
     __syncthreads();
     if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
@@ -957,6 +1171,10 @@ __global__ void __launch_bounds__(kThreads)
 // the kernels with the boundary variants (k_particle_ext.cu)
 cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm);
 cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,
+                                 cudaStream_t s);
+// the TSC kernels (k_particle_tsc.cu), boundary variants included
+cudaError_t particle_tsc_setup(int dims, size_t smem, int *ctas_per_sm);
+cudaError_t launch_particles_tsc(const ParticleLaunch &pl, int nctas, size_t smem,
                                  cudaStream_t s);
 
 }  // namespace pic

@@ -119,16 +119,18 @@ pic_status setup_tiles(pic_sim *s) {
         if (T < 1) return fail(s, PIC_EINVAL, "tile dims must be >= 1");
         tp.T[a] = T;
         tp.nt[a] = (s->g.n[a] + T - 1) / T;
-        tp.box[a] = (a == 2 && dims == 2) ? 1 : T + 5;
+        // staged box: the tile plus a halo of 2 cells (3 for TSC shapes)
+        const int halo = s->shape_order == 2 ? 3 : 2;
+        tp.box[a] = (a == 2 && dims == 2) ? 1 : T + 2 * halo + 1;
     }
     tp.ntiles = tp.nt[0] * tp.nt[1] * tp.nt[2];
     tp.boxn = tp.box[0] * tp.box[1] * tp.box[2];
     s->psmem = particle_smem_bytes(tp);
     if (s->psmem > 227 * 1024 - 1024)
         return fail(s, PIC_EINVAL, "particle tile too large for shared memory");
-    int per_sm = 0, per_sm_ext = 0;
-    CK(s, particle_kernel_setup(dims, s->psmem, &per_sm, &per_sm_ext));
-    if (per_sm < 1 || per_sm_ext < 1)
+    int per_sm = 0, per_sm_ext = 0, per_sm_tsc = 0;
+    CK(s, particle_kernel_setup(dims, s->psmem, &per_sm, &per_sm_ext, &per_sm_tsc));
+    if (per_sm < 1 || per_sm_ext < 1 || per_sm_tsc < 1)
         return fail(s, PIC_EINVAL, "particle tile does not fit on an SM");
     // beside the field work, one CTA per SM fewer leaves it room (3 of 4 measured best)
     const int use_sm = (!s->tun.no_overlap && per_sm > 1) ? per_sm - 1 : per_sm;
@@ -136,6 +138,11 @@ pic_status setup_tiles(pic_sim *s) {
     s->particle_ctas = s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm * s->num_sms;
     s->particle_ctas_ext =
         s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm_ext * s->num_sms;
+    // the TSC kernel holds ~127 registers a thread: 2 CTAs fill an SM's
+    // registers, so none is held back for the B pass
+    const int use_sm_tsc = (!s->tun.no_overlap && per_sm_tsc > 2) ? per_sm_tsc - 1 : per_sm_tsc;
+    s->particle_ctas_tsc =
+        s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm_tsc * s->num_sms;
     // tile-indexed buffers
     dfree(s, s->active);
     dfree(s, s->nactive);
@@ -317,6 +324,7 @@ ParticleLaunch particle_params(pic_sim *s) {
     P.diff_key[0] = (uint32_t)s->diff_seed;
     P.diff_key[1] = (uint32_t)(s->diff_seed >> 32);
     P.rng_step = (uint32_t)s->steps;
+    P.shape = s->shape_order;
     P.jdirty = s->jdirty;
     P.nbx = s->nbx;
     P.nby = s->nby;
@@ -338,6 +346,7 @@ bool alloc_external_field(pic_sim *s) {
 }
 
 int particle_ctas_for(const pic_sim *s, const ParticleLaunch &P) {
+    if (P.shape == 2) return s->particle_ctas_tsc;
     return particle_launch_ext(P) ? s->particle_ctas_ext : s->particle_ctas;
 }
 
@@ -609,6 +618,15 @@ pic_status pic_set_work_function(pic_sim *s, double W_eV) {
     return PIC_OK;
 }
 
+pic_status pic_set_shape_order(pic_sim *s, int order) {
+    if (!s) return fail(s, PIC_EINVAL, "null handle");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (order != 1 && order != 2) return fail(s, PIC_EINVAL, "order must be 1 (CIC) or 2 (TSC)");
+    if (s->nsp > 0) return fail(s, PIC_ESTATE, "set the shape order before loading species");
+    s->shape_order = order;
+    return setup_tiles(s);  // the staged box grows by a cell on each side for TSC
+}
+
 pic_status pic_set_particle_bc(pic_sim *s, int edges, double p_diffuse, uint64_t seed) {
     if (!s) return fail(s, PIC_EINVAL, "null handle");
     if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
@@ -830,11 +848,12 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
                     if (!alloc_zero(s, &zero[a], n)) return fail(s, PIC_ENOMEM, "bg");
                     at.disp[a] = zero[a];
                 }
-                CK(s, launch_rho_deposit(g, at, -d->q * weight / V, s->rho_bg, s->stream));
+                CK(s, launch_rho_deposit(g, at, -d->q * weight / V, 1, s->rho_bg, s->stream));
                 CK(s, cudaStreamSynchronize(s->stream));
                 for (int a = 0; a < 3; ++a) dfree(s, zero[a]);
             } else {
-                CK(s, launch_rho_deposit(g, at, -d->q * weight / V, s->rho_bg, s->stream));
+                CK(s, launch_rho_deposit(g, at, -d->q * weight / V, s->shape_order, s->rho_bg,
+                                         s->stream));
             }
         } else {
             CK(s, launch_add_uniform(s->rho_bg, g.ncell, -d->q * weight * n / (V * g.ncell),
@@ -1097,7 +1116,8 @@ pic_status pic_diagnostics(pic_sim *s, pic_diag *out) {
     for (int i = 0; i < s->nsp; ++i) {
         Species &sp = s->sp[i];
         CK(s, launch_rho_deposit(g, species_params(s, sp, sp.cur), sp.desc.q * sp.weight / V,
-                                 s->rho, s->stream));
+                                 sp.desc.kind == PIC_BOUND ? 1 : s->shape_order, s->rho,
+                                 s->stream));
     }
     CK(s, launch_gauss(g, E, s->inv_eps, s->rho, s->rho_bg, s->diag_acc, s->stream));
     DiagAcc acc;

@@ -319,6 +319,8 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (s->Eext[0] || s->p_diffuse > 0.0)
         return gfail(g, PIC_EINVAL,
                      "a simulation with an external field or diffuse reflection steps alone");
+    if (s->shape_order != 1)
+        return gfail(g, PIC_EINVAL, "a simulation with TSC shapes steps alone");
     for (int k = 0; k < s->nsp; ++k) {
         const double *gm = s->sp[k].desc.gamma;
         if (s->sp[k].desc.kind == PIC_BOUND && !(gm[0] == gm[1] && gm[1] == gm[2]))

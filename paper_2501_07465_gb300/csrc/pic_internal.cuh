@@ -143,7 +143,7 @@ struct TileP {
     int T[3];        // tile dims (cells)
     int nt[3];       // tiles per axis
     int ntiles;
-    int box[3];      // staged box dims = T + 5 (3D) / T + 5, T + 5, 1 (2D)
+    int box[3];      // staged box dims = T + 5 (3D) / T + 5, T + 5, 1 (2D); T + 7 for TSC
     int boxn;        // product
 };
 
@@ -163,6 +163,7 @@ struct ParticleLaunch {
     float p_diffuse;         // probability of a diffuse material-edge reflection
     uint32_t diff_key[2];    // Philox key of the diffuse draws
     uint32_t rng_step;       // step index of this particle phase (mod 2^32)
+    int shape;               // free / Dirac shape order: 1 CIC, 2 TSC (bound: CIC)
     uint8_t *jdirty;
     int nbx, nby, nbz, zchunk;
     const int *active;       // active tile list, largest particle count first
@@ -205,7 +206,8 @@ cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const 
 size_t particle_smem_bytes(const TileP &tp);
 // ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
 // variants (external field, diffuse reflection)
-cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext);
+cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext,
+                                  int *ctas_per_sm_tsc = nullptr);
 // true when the launch needs the kernel with the boundary variants (or the
 // anisotropic bound push)
 inline bool particle_launch_ext(const ParticleLaunch &pl) {
@@ -288,7 +290,8 @@ cudaError_t launch_energy_histogram(const SpeciesP &sp, double half_m, double e_
                                     unsigned long long *out, cudaStream_t s);
 cudaError_t launch_field_energy(const GridP &g, const float *const *E, const float *const *B,
                                 DiagAcc *acc, cudaStream_t s);
-cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V,
+// order: 1 CIC, 2 TSC
+cudaError_t launch_rho_deposit(const GridP &g, const SpeciesP &sp, double qw_over_V, int order,
                                double *rho, cudaStream_t s);
 cudaError_t launch_gauss(const GridP &g, const float *const *E, const float *inv_eps,
                          const double *rho, const double *rho_bg, DiagAcc *acc, cudaStream_t s);

@@ -64,6 +64,7 @@ struct pic_sim {
     int open_edges = 0;        // 1: particles cross material edges
     double p_diffuse = 0.0;    // share of diffuse material-edge reflections
     uint64_t diff_seed = 0;    // Philox key of the diffuse draws
+    int shape_order = 1;       // free and Dirac particles: 1 CIC, 2 TSC
     std::vector<uint8_t> mask_h;
     uint8_t *jdirty = nullptr;
     int nbx = 1, nby = 1, nbz = 1;
@@ -79,6 +80,7 @@ struct pic_sim {
     int **starts_dev = nullptr;
     int particle_ctas = 1;
     int particle_ctas_ext = 1;  // the same for the kernel with the boundary variants
+    int particle_ctas_tsc = 1;  // and for the TSC kernel
     size_t psmem = 0;
     int nsp = 0;
     pic::Species sp[kMaxSpecies];

@@ -98,6 +98,7 @@ SIGNATURES = {
                                          C.POINTER(C.c_double), C.c_size_t]),
     "pic_set_work_function": (C.c_int, [_H, C.c_double]),
     "pic_set_particle_bc": (C.c_int, [_H, C.c_int, C.c_double, C.c_uint64]),
+    "pic_set_shape_order": (C.c_int, [_H, C.c_int]),
     "pic_load_species": (C.c_int, [_H, C.POINTER(pic_species_desc), C.POINTER(pic_particles),
                                    C.POINTER(C.c_int)]),
     "pic_set_tuning": (C.c_int, [_H, C.POINTER(pic_tuning)]),
@@ -250,6 +251,12 @@ def pic_set_external_field(h, E):
 def pic_set_work_function(h, W_eV):
     """The work-function barrier of height W_eV built from the mask."""
     _check(load_library().pic_set_work_function(h, float(W_eV)), h)
+
+
+def pic_set_shape_order(h, order):
+    """1 CIC (default), 2 TSC for the free and Dirac particles (before
+    loading species)."""
+    _check(load_library().pic_set_shape_order(h, int(order)), h)
 
 
 def pic_set_particle_bc(h, edges=0, p_diffuse=0.0, seed=0):

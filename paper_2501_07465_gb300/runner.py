@@ -15,12 +15,15 @@ def grid_desc(wl):
                          pml_cells=g.get("pml_cells", 0), src=g.get("src"))
 
 
-def make_sim(wl, stream=0, tuning=None):
-    """A loaded simulation handle for workload `wl` on CUDA stream `stream`."""
+def make_sim(wl, stream=0, tuning=None, shape_order=1):
+    """A loaded simulation handle for workload `wl` on CUDA stream `stream`
+    (free and Dirac particles with CIC, or TSC for shape_order 2)."""
     h = pic.pic_create(grid_desc(wl), stream)
     try:
         if tuning:
             pic.pic_set_tuning(h, **tuning)
+        if shape_order != 1:
+            pic.pic_set_shape_order(h, shape_order)
         if wl.get("mask") is not None:
             pic.pic_set_material_mask(h, wl["mask"])
         for sp in wl["species"]:

@@ -65,8 +65,8 @@ MUTATIONS = [
     ("node vacuum fraction cell offset", "int c[3] = {i - 1 + di, j - 1 + dj,",
      "int c[3] = {i + di, j - 1 + dj,", "test_work_function_planar_barrier_closed_form"),
     ("external field on the B stagger",
-     "if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_E[c], X);",
-     "if (s->Eext[c]) E[c] += interp(s, s->Eext[c], STAG_B[c], X);",
+     "if (s->Eext[c]) E[c] += interp(s, order, s->Eext[c], STAG_E[c], X);",
+     "if (s->Eext[c]) E[c] += interp(s, order, s->Eext[c], STAG_B[c], X);",
      "test_external_field_gather_is_exact_for_linear_fields"),
     ("open edges ignored", "int edge = !outside && !s->open_edges &&", "int edge = !outside &&",
      "test_open_edges_let_particles_leave"),
