@@ -471,7 +471,17 @@ def run_relax_leg(args):
     readbacks between chunks are outside the timed group steps)."""
     from paper_2501_07465_gb300 import relax
     r = relax.run(t_end_fs=args.relax_fs, samples=20)
-    return {"workload": "FD relaxation: 2 nm periodic bulk cubes, 0.2 nm cells, T0 = 0.0375 eV, "
+    # the same 6e28 m^-3 cases at 32 and 128 ppc with TSC shapes (lower
+    # shape noise), stepped one after another
+    rt = relax.run(densities=(6e28,), ppcs=(32, 128), t_end_fs=args.relax_fs, samples=20,
+                   shape_order=2)
+    tsc = {"shape": "TSC", "wall_s": rt["wall_s"],
+           "particle_steps_per_s": rt["particle_steps_per_s"],
+           "cases": [{"density": c["density"], "ppc": c["ppc"],
+                      "A_eV_per_sqrt_fs": finite(c["A_eV_per_sqrt_fs"], 5),
+                      "r2": finite(c["r2"], 4), "beta_end_eV": finite(c["beta_eV"][-1], 5)}
+                     for c in rt["cases"]]}
+    return {"tsc": tsc,"workload": "FD relaxation: 2 nm periodic bulk cubes, 0.2 nm cells, T0 = 0.0375 eV, "
                         "n = 2/4/6e28 m^-3 x 16/32/64/128 ppc, one batch group",
             "steps": r["steps"], "t_end_fs": args.relax_fs, "tile": r["tile"],
             "wall_s": r["wall_s"], "particle_steps_per_s": r["particle_steps_per_s"],
