@@ -15,7 +15,6 @@ The growth law is fitted as beta(t) = A sqrt(t) over the samples t > 0.
 """
 from __future__ import annotations
 
-import math
 import time
 
 import numpy as np

@@ -2,7 +2,6 @@
 histogram (integer work: bit-exact against the oracle on the same
 velocities), the tail temperature at loading against the Fermi-Dirac law,
 and the numerical heating of a bulk cube against the oracle."""
-import math
 
 import numpy as np
 import pytest
