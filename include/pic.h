@@ -102,8 +102,7 @@ typedef struct pic_grid_desc {
    damping of PIC_BOUND per axis (Eq. modlorentz with diagonal tensors;
    gamma finite and >= 0, PIC_EINVAL otherwise; unequal gamma entries take
    the general 3x3 solve of the modified Boris rotation in the kernel with
-   the boundary variants, and such a simulation steps alone: pic_group_add
-   refuses it).  v_F: Fermi velocity of PIC_DIRAC (m is then the averaged
+   the boundary variants, single or batch).  v_F: Fermi velocity of PIC_DIRAC (m is then the averaged
    transverse mass p_F / (2 v_F) of Sec. 5).  background: PIC_BG_*. */
 typedef struct pic_species_desc {
     int kind;
@@ -232,7 +231,8 @@ pic_status pic_set_permittivity(pic_sim *sim, const float *eps_r, size_t n);
    Gauss diagnostic).  ex, ey, ez: n = number of cells finite doubles each,
    [nz][ny][nx] (PIC_EINVAL otherwise); the library keeps an FP32 copy, read
    back with PIC_EXT* in pic_read_fields.  ex == NULL removes the field.
-   Such a simulation steps alone (pic_group_add refuses it). */
+   Not while the simulation belongs to a group (PIC_ESTATE); a member with a
+   field steps in its group with the variant batch kernel. */
 pic_status pic_set_external_field(pic_sim *sim, const double *ex, const double *ey,
                                   const double *ez, size_t n);
 
@@ -267,7 +267,8 @@ pic_status pic_set_work_function(pic_sim *sim, double W_eV);
    be 0.
    Non-periodic domain faces reflect specularly under either rule.  edges
    outside the enum or p_diffuse outside [0, 1]: PIC_EINVAL.  A simulation
-   with p_diffuse > 0 steps alone (pic_group_add refuses it). */
+   with p_diffuse > 0 steps alone (pic_group_add refuses it: a captured
+   group epoch would not advance the draws' step index). */
 pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64_t seed);
 
 /* Shape function W of Sec. 4.1 for the free and Dirac particles: order 1

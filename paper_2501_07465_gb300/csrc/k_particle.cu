@@ -58,7 +58,10 @@ cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *
 
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
                                   const int *active, const int2 *items, int nitems, int *sched,
-                                  int nctas, size_t smem, cudaStream_t s) {
+                                  int nctas, size_t smem, bool ext, cudaStream_t s) {
+    if (ext)
+        return launch_batch_particles_ext(dims, descs, fpar, active, items, nitems, sched, nctas,
+                                          smem, s);
     if (nctas < 1) nctas = 1;
     if (dims == 3)
         batch_particle_kernel<3><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems,

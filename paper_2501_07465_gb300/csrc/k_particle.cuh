@@ -1124,7 +1124,9 @@ __global__ void __launch_bounds__(kThreads, 4) particle_kernel_ext(ParticleLaunc
 // Many simulations in one persistent launch: items[i] = (simulation, tile),
 // tile < 0 = padding.  Each simulation's parameter block (two variants, one
 // per field ping-pong parity) is copied to shared memory for its items.
-template <int DIM>
+// X: the variant with the external field and the anisotropic bound push
+// (k_particle_ext.cu), launched when a member has either.
+template <int DIM, bool X = false>
 __global__ void __launch_bounds__(kThreads)
     batch_particle_kernel(const ParticleLaunch *descs, const int *fpar, const int *active,
                           const int2 *items, int nitems, int *sched) {
@@ -1151,7 +1153,7 @@ __global__ void __launch_bounds__(kThreads)
         if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
         __syncthreads();
         if (threadIdx.x == 0) s_sim = w.x;
-        tile_pass<DIM, false>(sP, w.y, smem, s_refl);
+        tile_pass<DIM, X>(sP, w.y, smem, s_refl);
         __syncthreads();
         if (threadIdx.x < sP.nsp && s_refl[threadIdx.x])
             atomicAdd(sP.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
@@ -1172,6 +1174,11 @@ __global__ void __launch_bounds__(kThreads)
 cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm);
 cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,
                                  cudaStream_t s);
+// the batch kernel with the external field and the anisotropic bound push
+// (k_particle_ext.cu)
+cudaError_t launch_batch_particles_ext(int dims, const ParticleLaunch *descs, const int *fpar,
+                                       const int *active, const int2 *items, int nitems,
+                                       int *sched, int nctas, size_t smem, cudaStream_t s);
 // the TSC kernels (k_particle_tsc.cu), boundary variants included
 cudaError_t particle_tsc_setup(int dims, size_t smem, int *ctas_per_sm);
 cudaError_t launch_particles_tsc(const ParticleLaunch &pl, int nctas, size_t smem,

@@ -1,6 +1,7 @@
 // k_particle_ext.cu -- the particle kernels with the boundary variants of
-// Sec. 3 (external electrostatic field, diffuse reflection), instantiated
-// apart from the plain ones so that the two compile in parallel.
+// Sec. 3 (external electrostatic field, diffuse reflection) and the
+// anisotropic bound push, single-simulation and batch, instantiated apart
+// from the plain ones so that the two compile in parallel.
 #include "k_particle.cuh"
 
 namespace pic {
@@ -12,6 +13,9 @@ cudaError_t ext_setup_dim(size_t smem, int *ctas_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(particle_kernel_ext<DIM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(batch_particle_kernel<DIM, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel_ext<DIM>,
                                                          kThreads, smem);
 }
@@ -20,6 +24,19 @@ cudaError_t ext_setup_dim(size_t smem, int *ctas_per_sm) {
 
 cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm) {
     return dims == 3 ? ext_setup_dim<3>(smem, ctas_per_sm) : ext_setup_dim<2>(smem, ctas_per_sm);
+}
+
+cudaError_t launch_batch_particles_ext(int dims, const ParticleLaunch *descs, const int *fpar,
+                                       const int *active, const int2 *items, int nitems,
+                                       int *sched, int nctas, size_t smem, cudaStream_t s) {
+    if (nctas < 1) nctas = 1;
+    if (dims == 3)
+        batch_particle_kernel<3, true><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items,
+                                                                     nitems, sched);
+    else
+        batch_particle_kernel<2, true><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items,
+                                                                     nitems, sched);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,

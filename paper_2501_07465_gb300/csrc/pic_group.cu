@@ -28,6 +28,7 @@ struct pic_group {
     int sort_interval = 32;
     size_t psmem = 0;
     int pctas = 1;
+    bool ext = false;  // some member has an external field or anisotropic gamma
     std::vector<pic_sim *> slots;
     std::vector<long long> done, target;  // host mirrors
     bool dirty = true;
@@ -129,6 +130,7 @@ pic_status rebuild(pic_group *g) {
     std::vector<SimTiles> hsims;
     long long total = 0;
     int ioff = 0;
+    bool ext = false;
     for (int k = 0; k < cap; ++k) {
         pic_sim *s = g->slots[k];
         if (!s) continue;
@@ -137,6 +139,7 @@ pic_status rebuild(pic_group *g) {
             s->fcur = par;
             hp[2 * k + par] = pic::particle_params(s);
             hp[2 * k + par].step_counter = nullptr;  // begin_step sets the counter
+            ext = ext || pic::particle_launch_ext(hp[2 * k + par]);
             hf[2 * k + par] = pic::field_params(s);
         }
         s->fcur = keep;
@@ -211,6 +214,7 @@ pic_status rebuild(pic_group *g) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream)
                      : cudaSuccess;
     };
+    g->ext = ext;
     GCK(g, up(g->pdesc, hp.data(), hp.size() * sizeof(ParticleLaunch)));
     GCK(g, up(g->grids, hg.data(), hg.size() * sizeof(GridP)));
     GCK(g, up(g->fdesc, hf.data(), hf.size() * sizeof(FieldP)));
@@ -251,7 +255,8 @@ pic_status enqueue_step(pic_group *g) {
     GCK(g, pic::launch_begin_step(g->capacity, g->member, g->active, g->fpar, g->ddone, g->dtarget,
                                   g->counters, g->stream));
     GCK(g, pic::launch_batch_particles(g->dims, g->pdesc, g->fpar, g->active, g->pitems,
-                                       g->npitems, g->psched, g->pctas, g->psmem, g->stream));
+                                       g->npitems, g->psched, g->pctas, g->psmem, g->ext,
+                                       g->stream));
     GCK(g, pic::launch_batch_field(g->dims, g->grids, g->fdesc, g->fpar, g->active, g->fitems,
                                    g->nfitems, g->stream));
     g->launches += 3;
@@ -316,23 +321,19 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (nsteps < 0) return gfail(g, PIC_EINVAL, "nsteps must be >= 0");
     if (s->inv_eps)
         return gfail(g, PIC_EINVAL, "a simulation with a permittivity steps alone (pic_step)");
-    if (s->Eext[0] || s->p_diffuse > 0.0)
-        return gfail(g, PIC_EINVAL,
-                     "a simulation with an external field or diffuse reflection steps alone");
+    // the diffuse draws take the step index from the host, which a captured
+    // epoch does not update
+    if (s->p_diffuse > 0.0)
+        return gfail(g, PIC_EINVAL, "a simulation with diffuse reflection steps alone");
     if (s->shape_order != 1)
         return gfail(g, PIC_EINVAL, "a simulation with TSC shapes steps alone");
-    for (int k = 0; k < s->nsp; ++k) {
-        const double *gm = s->sp[k].desc.gamma;
-        if (s->sp[k].desc.kind == PIC_BOUND && !(gm[0] == gm[1] && gm[1] == gm[2]))
-            return gfail(g, PIC_EINVAL, "a simulation with an anisotropic gamma steps alone");
-    }
     if (g->dims == 0) {
         g->dims = s->g.dims;
         for (int a = 0; a < 3; ++a) g->tile[a] = s->tp.T[a];
         g->sort_interval = std::max(1, s->tun.sort_interval);
         g->psmem = s->psmem;
-        int per_sm = 0;
-        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm, nullptr));
+        int per_sm = 0, per_sm_ext = 0;
+        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm, &per_sm_ext));
         g->pctas = std::max(1, per_sm) * s->num_sms;
     }
     if (s->g.dims != g->dims) return gfail(g, PIC_EINVAL, "members must share dims");

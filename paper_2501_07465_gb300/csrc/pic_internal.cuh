@@ -200,9 +200,11 @@ cudaError_t launch_field_b_tma(const GridP &g, const FieldP &f, const TmaMaps &m
 cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
                              int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
+// ext: launch the batch kernel with the external field and the anisotropic
+// bound push (some member has either)
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
                                   const int *active, const int2 *items, int nitems, int *sched,
-                                  int nctas, size_t smem, cudaStream_t s);
+                                  int nctas, size_t smem, bool ext, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
 // ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
 // variants (external field, diffuse reflection)

@@ -157,7 +157,7 @@ def test_anisotropic_medium_rings_per_axis(axis):
 
 def test_gamma_arguments():
     """Negative or NaN gamma entries are refused with PIC_EINVAL; a group
-    refuses a simulation with an anisotropic gamma."""
+    takes a simulation with an anisotropic gamma."""
     pic = _pic()
     n = (8, 8, 8)
     grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
@@ -174,9 +174,8 @@ def test_gamma_arguments():
         desc = pic.species_desc(I.BOUND, -I.QE, I.ME, 1.0, omega0=W0, gamma=GAMMA)
         pic.pic_load_species(h, desc, cell=cb, v=vb, anchor_off=anc, disp=disp)
         g = pic.pic_group_create(4)
-        with pytest.raises(pic.PicError) as e:
-            pic.pic_group_add(g, h, 1)
-        assert e.value.status == pic.PIC_EINVAL
+        pic.pic_group_add(g, h, 1)
+        pic.pic_group_remove(g, h)
     finally:
         if g is not None:
             pic.pic_group_destroy(g)

@@ -83,7 +83,7 @@ def test_boundary_variant_arguments():
     """Sizes, NaN / infinite fields, |W| > 1e3 eV, unknown edge rules,
     p outside [0, 1] and open edges with a diffuse share are refused with
     PIC_EINVAL; an external field round-trips at FP32; a group refuses a
-    simulation with an external field or a diffuse share."""
+    simulation with a diffuse share and takes one with an external field."""
     pic = _pic()
     n = (8, 8, 8)
     grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
@@ -113,8 +113,11 @@ def test_boundary_variant_arguments():
             pic.pic_write_fields(h, pic.PIC_EXTX, E[0])
         assert e.value.status == pic.PIC_EINVAL
         g = pic.pic_group_create(4)
-        with pytest.raises(pic.PicError):
-            pic.pic_group_add(g, h, 1)
+        pic.pic_group_add(g, h, 1)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_set_external_field(h, None)  # not while in a group
+        assert e.value.status == pic.PIC_ESTATE
+        pic.pic_group_remove(g, h)
         pic.pic_set_external_field(h, None)
         pic.pic_set_particle_bc(h, pic.PIC_EDGE_REFLECT, 0.5, 9)
         with pytest.raises(pic.PicError):
