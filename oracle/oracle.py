@@ -73,6 +73,9 @@ def _declare(L):
     L.orc_work_function_field.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp]
     L.orc_set_particle_bc.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64]
     L.orc_set_shape_order.argtypes = [C.c_void_p, C.c_int]
+    L.orc_set_binding_offdiag.argtypes = [C.c_void_p, C.c_int, _dp]
+    L.orc_push_bound_tensor.argtypes = [_dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                        _dp, _dp, _dp]
     L.orc_add_species.restype = C.c_int
     L.orc_add_species.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                                   _dp, C.c_double, C.c_long, _dp, _dp, _dp, C.c_int]
@@ -136,6 +139,20 @@ def push_bound(v, D, E, B, q, m, dt, omega0, gamma):
     _, pw = _d(np.broadcast_to(np.asarray(omega0, dtype=np.float64), (3,)).copy())
     _, pg = _d(np.broadcast_to(np.asarray(gamma, dtype=np.float64), (3,)).copy())
     lib().orc_push_bound(pv, pD, pE, pB, q, m, dt, pw, pg)
+    return v, D
+
+
+def push_bound_tensor(v, D, E, B, q, m, dt, omega0, w2off, gamma):
+    """push_bound with the binding tensor diag(omega0^2) + off-diagonal
+    w2off = (xy, xz, yz) in s^-2."""
+    v, pv = _d(np.array(v, dtype=np.float64))
+    D, pD = _d(np.array(D, dtype=np.float64))
+    _, pE = _d(E)
+    _, pB = _d(B)
+    _, pw = _d(np.broadcast_to(np.asarray(omega0, dtype=np.float64), (3,)).copy())
+    _, po = _d(np.asarray(w2off, dtype=np.float64).copy())
+    _, pg = _d(np.broadcast_to(np.asarray(gamma, dtype=np.float64), (3,)).copy())
+    lib().orc_push_bound_tensor(pv, pD, pE, pB, q, m, dt, pw, po, pg)
     return v, D
 
 
@@ -277,6 +294,12 @@ class OracleSim:
         out = [np.zeros(self.shape) for _ in range(3)]
         lib().orc_work_function_field(self._h, float(W_eV), *[a.ctypes.data_as(_dp) for a in out])
         return out
+
+    def set_binding_offdiag(self, k, w2off):
+        """Off-diagonal (xy, xz, yz) entries of bound species k's Omega^2 (s^-2)."""
+        a = np.ascontiguousarray(w2off, dtype=np.float64)
+        self._off = a
+        lib().orc_set_binding_offdiag(self._h, int(k), a.ctypes.data_as(_dp))
 
     def set_shape_order(self, order):
         """1 CIC, 2 TSC for the free and Dirac particles (before add_species)."""

@@ -64,6 +64,10 @@ typedef struct {
     int kind;
     double q, m, w;
     double omega0[3], gamma[3];
+    /* off-diagonal entries of the binding tensor Omega^2 (xy, xz, yz, s^-2;
+       the diagonal is omega0^2), used when has_off */
+    double w2off[3];
+    int has_off;
     double vF;
     long n;
     double *X; /* 3n: position (free, Dirac) or anchor (bound), cell units */
@@ -469,13 +473,34 @@ static double det3(const double M[3][3]) {
    i.e. (I + (dt/2)Gamma - eps(b)) v+ = (I - (dt/2)Gamma + eps(b)) v-, solved
    here by Cramer's rule; second kick; drift D += dt v (Eq. discrvel).
    D is the displacement from the anchor in metres. */
+/* The same with a full symmetric binding tensor: the Hooke term becomes
+   Omega^2 D with Omega^2 = diag(omega0^2) + the off-diagonal entries w2off
+   (xy, xz, yz); w2off == NULL is the diagonal case. */
+void orc_push_bound_tensor(double *v, double *D, const double *E, const double *B, double q,
+                           double m, double dt, const double *omega0, const double *w2off,
+                           const double *gamma);
+
 void orc_push_bound(double *v, double *D, const double *E, const double *B, double q, double m,
                     double dt, const double *omega0, const double *gamma) {
+    orc_push_bound_tensor(v, D, E, B, q, m, dt, omega0, NULL, gamma);
+}
+
+void orc_push_bound_tensor(double *v, double *D, const double *E, const double *B, double q,
+                           double m, double dt, const double *omega0, const double *w2off,
+                           const double *gamma) {
     double h = q * dt / (2.0 * m);
     double b[3] = {h * B[0], h * B[1], h * B[2]};
     double kick[3], vm[3];
     for (int a = 0; a < 3; ++a) {
-        kick[a] = 0.5 * dt * (q / m * E[a] - omega0[a] * omega0[a] * D[a]);
+        double hooke = omega0[a] * omega0[a] * D[a];
+        if (w2off) {
+            /* off-diagonal entries of row a: (0,1) xy, (0,2) xz, (1,2) yz */
+            const double o1 = a == 0 ? w2off[0] : a == 1 ? w2off[0] : w2off[1];
+            const double o2 = a == 0 ? w2off[1] : a == 1 ? w2off[2] : w2off[2];
+            const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+            hooke += o1 * D[b1] + o2 * D[b2];
+        }
+        kick[a] = 0.5 * dt * (q / m * E[a] - hooke);
         vm[a] = v[a] + kick[a];
     }
     /* matrix of u -> u x b */
@@ -564,6 +589,15 @@ static void gather(const orc_sim *s, int order, const double *X, double *E, doub
 void orc_gather(void *h, const double *X, double *E, double *B) {
     const orc_sim *s = (const orc_sim *)h;
     gather(s, s->shape_order, X, E, B);
+}
+
+/* Off-diagonal entries (xy, xz, yz, s^-2) of bound species k's binding
+   tensor Omega^2 (Eq. modlorentz with a full symmetric tensor; the diagonal
+   stays omega0^2). */
+void orc_set_binding_offdiag(void *h, int k, const double *w2off) {
+    orc_species *sp = &((orc_sim *)h)->sp[k];
+    for (int a = 0; a < 3; ++a) sp->w2off[a] = w2off[a];
+    sp->has_off = 1;
 }
 
 /* Shape order of the free and Dirac particles (1 CIC, 2 TSC); bound
@@ -858,7 +892,8 @@ static void push_species(orc_sim *s, orc_species *sp, int k) {
         gather(s, order, X0, E, B);
         if (sp->kind == KIND_BOUND) {
             double *D = &sp->D[3 * p];
-            orc_push_bound(v, D, E, B, sp->q, sp->m, dt, sp->omega0, sp->gamma);
+            orc_push_bound_tensor(v, D, E, B, sp->q, sp->m, dt, sp->omega0,
+                                  sp->has_off ? sp->w2off : NULL, sp->gamma);
             particle_pos(s, sp, p, X1);
         } else {
             if (sp->kind == KIND_FREE) orc_push_free(v, E, B, sp->q, sp->m, dt);

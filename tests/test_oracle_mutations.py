@@ -81,6 +81,9 @@ MUTATIONS = [
     ("2D law uniform in angle", "const double st = 2.0 * u1 - 1.0, ct = sqrt(1.0 - st * st);",
      "const double st = sin(PI * (u1 - 0.5)), ct = sqrt(1.0 - st * st);",
      "test_diffuse_reflection_of_dirac_carriers_is_2d_lambert"),
+    ("binding tensor row", "const double o2 = a == 0 ? w2off[1] : a == 1 ? w2off[2] : w2off[2];",
+     "const double o2 = a == 0 ? w2off[2] : a == 1 ? w2off[2] : w2off[2];",
+     "test_bound_binding_tensor_is_rotation_covariant"),
     ("TSC central weight", "if (r < 0.5) return 0.75 - r * r;", "if (r < 0.5) return 0.7 - r * r;",
      "test_tsc_weights_hand_computed or test_tsc_esirkepov_satisfies_continuity_exactly"),
     ("TSC node window", "return order == 2 ? (int)floor(X + 0.5) - 1 : (int)floor(X);",

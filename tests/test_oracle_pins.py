@@ -262,6 +262,32 @@ def test_bound_anisotropic_gamma():
         assert abs(rhs) > 1e-4 * (v0 @ v0)
 
 
+def test_bound_binding_tensor_is_rotation_covariant():
+    """A full symmetric binding tensor Omega^2 = R diag(w^2) R^T: pushing D
+    with it under a random drive E_n equals pushing R^T D with the diagonal
+    tensor under R^T E_n and rotating back (isotropic damping, B = 0, so the
+    rotation commutes with the scheme); a transposed or misplaced
+    off-diagonal entry breaks this."""
+    q, m, dt = -QE, ME, 4.81e-19
+    w = np.array([4.7e15, 3.1e15, 6.0e15])
+    a, b = 0.7, -0.4
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    R = Rz @ Rx
+    W2 = R @ np.diag(w ** 2) @ R.T
+    omega0 = np.sqrt(np.diag(W2))
+    off = np.array([W2[0, 1], W2[0, 2], W2[1, 2]])
+    g = np.array([2e14] * 3)
+    v, D = np.zeros(3), np.zeros(3)
+    vr, Dr = np.zeros(3), np.zeros(3)
+    for n in range(300):
+        E = RNG.normal(size=3) * 1e9
+        v, D = O.push_bound_tensor(v, D, E, np.zeros(3), q, m, dt, omega0, off, g)
+        vr, Dr = O.push_bound(vr, Dr, R.T @ E, np.zeros(3), q, m, dt, w, g)
+        np.testing.assert_allclose(D, R @ Dr, rtol=0, atol=1e-9 * np.abs(D).max())
+        np.testing.assert_allclose(v, R @ vr, rtol=0, atol=1e-9 * np.abs(v).max())
+
+
 def test_bound_push_reduces_to_boris_when_unbound():
     """gamma = 0, w0 = 0: the gyrotropic solve equals the Boris rotation."""
     q, m, dt = -QE, ME, 1e-16
