@@ -282,6 +282,17 @@ pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64
    (pic_group_add refuses it). */
 pic_status pic_set_shape_order(pic_sim *sim, int order);
 
+/* Full symmetric binding tensor of bound species `species` (Eq. modlorentz
+   with a tensor restoring force): Omega^2 = diag(omega0^2) plus the
+   off-diagonal entries w2off = (xy, xz, yz) in s^-2, so the Hooke term of
+   the push is Omega^2 D (a rotated anisotropic medium).  The tensor must be
+   positive definite and finite (PIC_EINVAL), dt within the limit of Eq.
+   dtlimit with the largest eigenvalue (bounded by Gershgorin's discs) as
+   the binding frequency squared (PIC_EDTLIMIT), the species bound
+   (PIC_EINVAL), the simulation not in a group (PIC_ESTATE).  Such a species runs in the kernel with the boundary
+   variants (single or batch). */
+pic_status pic_set_binding_tensor(pic_sim *sim, int species, const double *w2off);
+
 /* Add a species (explicit particles or the Fermi-Dirac loader) and sort it
    into tiles.  Re-checks Eq. dtlimit with the plasma and binding frequencies
    of all species so far (PIC_EDTLIMIT).  *species_id receives its index. */

@@ -498,6 +498,12 @@ __device__ inline void bound_push(float *v, float *D, const float *E, const floa
     float k0 = h * E[0] - s.hw0sq[0] * D[0];
     float k1 = h * E[1] - s.hw0sq[1] * D[1];
     float k2 = h * E[2] - s.hw0sq[2] * D[2];
+    if (X && s.tensor) {
+        // off-diagonal entries of the binding tensor (xy, xz, yz) x dt / 2
+        k0 -= s.hw0off[0] * D[1] + s.hw0off[1] * D[2];
+        k1 -= s.hw0off[0] * D[0] + s.hw0off[2] * D[2];
+        k2 -= s.hw0off[1] * D[0] + s.hw0off[2] * D[1];
+    }
     float vm0 = v[0] + k0, vm1 = v[1] + k1, vm2 = v[2] + k2;
     float b0 = h * B[0], b1 = h * B[1], b2 = h * B[2];
     if (X && s.aniso) {

@@ -184,6 +184,8 @@ SpeciesP species_params(const pic_sim *s, const Species &sp, int buf) {
     p.gdt2 = (float)(0.5 * d.gamma[0] * dt);
     for (int a = 0; a < 3; ++a) p.gdt2v[a] = (float)(0.5 * d.gamma[a] * dt);
     p.aniso = d.kind == PIC_BOUND && !(d.gamma[0] == d.gamma[1] && d.gamma[1] == d.gamma[2]);
+    for (int a = 0; a < 3; ++a) p.hw0off[a] = (float)(0.5 * dt * sp.w2off[a]);
+    p.tensor = sp.has_off ? 1 : 0;
     p.vF = (float)d.v_F;
     p.dt = (float)dt;
     const double qw = d.q * sp.weight;
@@ -615,6 +617,32 @@ pic_status pic_set_work_function(pic_sim *s, double W_eV) {
     if (!alloc_external_field(s)) return fail(s, PIC_ENOMEM, "external field");
     CK(s, launch_work_function(s->g, s->mask_d, W_eV, s->Eext, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+pic_status pic_set_binding_tensor(pic_sim *s, int k, const double *w2off) {
+    if (!s || !w2off) return fail(s, PIC_EINVAL, "null argument");
+    if (s->group) return fail(s, PIC_ESTATE, "the simulation belongs to a group");
+    if (k < 0 || k >= s->nsp || s->sp[k].desc.kind != PIC_BOUND)
+        return fail(s, PIC_EINVAL, "not a bound species");
+    const double *w0 = s->sp[k].desc.omega0;
+    const double xx = w0[0] * w0[0], yy = w0[1] * w0[1], zz = w0[2] * w0[2];
+    const double xy = w2off[0], xz = w2off[1], yz = w2off[2];
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(w2off[a])) return fail(s, PIC_EINVAL, "entries must be finite");
+    // positive definite (Sylvester): a restoring force in every direction
+    const double m2 = xx * yy - xy * xy;
+    const double m3 = xx * (yy * zz - yz * yz) - xy * (xy * zz - yz * xz) + xz * (xy * yz - yy * xz);
+    if (!(xx > 0 && m2 > 0 && m3 > 0))
+        return fail(s, PIC_EINVAL, "the binding tensor must be positive definite");
+    // Eq. dtlimit with the largest eigenvalue bounded by Gershgorin's discs
+    const double lam = std::max({xx + std::fabs(xy) + std::fabs(xz),
+                                 yy + std::fabs(xy) + std::fabs(yz),
+                                 zz + std::fabs(xz) + std::fabs(yz)});
+    if (!(dt_limit(s, std::max(s->omega_b2, lam), s->omega_p2) > s->gd.dt))
+        return fail(s, PIC_EDTLIMIT, "dt exceeds the stability limit of Eq. dtlimit with this tensor");
+    for (int a = 0; a < 3; ++a) s->sp[k].w2off[a] = w2off[a];
+    s->sp[k].has_off = true;
     return PIC_OK;
 }
 

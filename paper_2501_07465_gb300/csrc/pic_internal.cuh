@@ -77,6 +77,8 @@ struct SpeciesP {
     float gdt2;                   // gamma dt / 2 (isotropic gamma)
     float gdt2v[3];               // gamma_a dt / 2 per axis
     int aniso;                    // bound with unequal gamma entries: the general solve
+    float hw0off[3];              // (dt/2) x off-diagonal binding tensor entries (xy, xz, yz)
+    int tensor;                   // bound with a full binding tensor
     float vF;
     float dt;
     float dtd[3];                 // dt / d_a
@@ -214,7 +216,7 @@ cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *
 // anisotropic bound push)
 inline bool particle_launch_ext(const ParticleLaunch &pl) {
     bool aniso = false;
-    for (int i = 0; i < pl.nsp; ++i) aniso = aniso || pl.sp[i].aniso;
+    for (int i = 0; i < pl.nsp; ++i) aniso = aniso || pl.sp[i].aniso || pl.sp[i].tensor;
     return pl.Eext[0] != nullptr || pl.p_diffuse > 0.f || aniso;
 }
 

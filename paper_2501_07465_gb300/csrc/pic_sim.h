@@ -28,6 +28,8 @@ struct Species {
     float *disp[2][3] = {};
     int *tile_start = nullptr;
     unsigned long long *nrefl = nullptr;
+    double w2off[3] = {0, 0, 0};  // off-diagonal binding tensor entries (xy, xz, yz), s^-2
+    bool has_off = false;
 };
 
 struct TimedEvents {

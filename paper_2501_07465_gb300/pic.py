@@ -99,6 +99,7 @@ SIGNATURES = {
     "pic_set_work_function": (C.c_int, [_H, C.c_double]),
     "pic_set_particle_bc": (C.c_int, [_H, C.c_int, C.c_double, C.c_uint64]),
     "pic_set_shape_order": (C.c_int, [_H, C.c_int]),
+    "pic_set_binding_tensor": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double)]),
     "pic_load_species": (C.c_int, [_H, C.POINTER(pic_species_desc), C.POINTER(pic_particles),
                                    C.POINTER(C.c_int)]),
     "pic_set_tuning": (C.c_int, [_H, C.POINTER(pic_tuning)]),
@@ -251,6 +252,13 @@ def pic_set_external_field(h, E):
 def pic_set_work_function(h, W_eV):
     """The work-function barrier of height W_eV built from the mask."""
     _check(load_library().pic_set_work_function(h, float(W_eV)), h)
+
+
+def pic_set_binding_tensor(h, k, w2off):
+    """Off-diagonal entries (xy, xz, yz, s^-2) of bound species k's binding
+    tensor; the diagonal stays omega0^2."""
+    a = np.ascontiguousarray(w2off, dtype=np.float64).ravel()
+    _check(load_library().pic_set_binding_tensor(h, int(k), _ptr(a, C.c_double)), h)
 
 
 def pic_set_shape_order(h, order):

@@ -180,3 +180,85 @@ def test_gamma_arguments():
         if g is not None:
             pic.pic_group_destroy(g)
         pic.pic_destroy(h)
+
+
+def _rotated_tensor():
+    """Omega^2 = R diag(W0^2) R^T for a rotation about z then x: the diagonal
+    (as omega0) and the off-diagonal entries (xy, xz, yz)."""
+    a, b = 0.7, -0.4
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    R = Rz @ Rx
+    W2 = R @ np.diag(np.array(W0) ** 2) @ R.T
+    return tuple(np.sqrt(np.diag(W2))), np.array([W2[0, 1], W2[0, 2], W2[1, 2]])
+
+
+@pytest.mark.parametrize("overlap", [1, 0])
+def test_binding_tensor_matches_oracle(overlap):
+    """Bound electrons with a full (rotated) binding tensor in the driven
+    metal sphere: one step particle by particle (1e-5), 30 more steps in the
+    fields (1e-3) and 99 % of the bound velocities (1e-4)."""
+    rng = np.random.default_rng(63)
+    omega0, off = _rotated_tensor()
+    grid, mask, species = PR.sphere_case(rng, omega0=omega0, gamma=GAMMA)
+    species = PR.guarded_species(grid, mask, species, lambda s: s.set_binding_offdiag(1, off))
+    pic = _pic()
+    s = PR.oracle_sim(grid, mask, species)
+    s.set_binding_offdiag(1, off)
+    h = PR.gpu_sim(grid, mask, species, tuning=dict(no_overlap=1 - overlap, field_mode=2))
+    pic.pic_set_binding_tensor(h, 1, off)
+    try:
+        PR.compare_one_step(pic, h, s, grid, species)
+        pic.pic_step(h, 30)
+        s.step(30)
+        got = PR.gpu_fields(h, grid)
+        for c in range(6):
+            assert PR.rel_l2(got[c], s.field(c)) < 1e-3, c
+        _, Vb, _, _ = s.species(1)
+        rb = pic.pic_read_species(h, 1, species[1]["cell"].size, bound=True)
+        rel = np.linalg.norm(rb["v"] - Vb, axis=1) / np.maximum(np.linalg.norm(Vb, axis=1), 1e3)
+        assert np.quantile(rel, 0.99) < 1e-4
+    finally:
+        pic.pic_destroy(h)
+        s.close()
+
+
+def test_binding_tensor_arguments():
+    """A tensor that is not positive definite, NaN entries or a free species
+    are refused (PIC_EINVAL); a tensor too stiff for dt (Eq. dtlimit with the
+    Gershgorin bound of its largest eigenvalue) gives PIC_EDTLIMIT."""
+    pic = _pic()
+    n = (8, 8, 8)
+    grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
+    rng = np.random.default_rng(7)
+    cb, anc, disp, vb = I.random_bound(rng, n, 50)
+    cell, off, v = I.random_particles(rng, n, 50)
+    h = PR.gpu_sim(grid, None, [])
+    try:
+        pic.pic_load_species(h, pic.species_desc(I.FREE, -I.QE, I.ME, 1.0), cell=cell, off=off,
+                             v=v)
+        pic.pic_load_species(h, pic.species_desc(I.BOUND, -I.QE, I.ME, 1.0, omega0=W0,
+                                                 gamma=GAMMA),
+                             cell=cb, v=vb, anchor_off=anc, disp=disp)
+        w = np.array(W0) ** 2
+        for k, bad in ((1, [w[0], 0, 0]), (1, [0, float("nan"), 0]), (0, [1e30, 0, 0])):
+            with pytest.raises(pic.PicError) as e:
+                pic.pic_set_binding_tensor(h, k, bad)
+            assert e.value.status == pic.PIC_EINVAL
+        pic.pic_set_binding_tensor(h, 1, [0.5 * math.sqrt(w[0] * w[1]), 0, 0])  # accepted
+    finally:
+        pic.pic_destroy(h)
+    # stiff binding: omega0 = 1.3e18 s^-1 loads (Eq. dtlimit: 1.2e-18 s >
+    # dt), but with all off-diagonal entries 0.9 omega0^2 (positive
+    # definite, eigenvalues 2.8 and 0.1 omega0^2) the limit drops to
+    # 8.3e-19 s
+    h = PR.gpu_sim(grid, None, [])
+    try:
+        w0 = 1.3e18
+        pic.pic_load_species(h, pic.species_desc(I.BOUND, -I.QE, I.ME, 1.0, omega0=(w0,) * 3),
+                             cell=cb, v=vb, anchor_off=anc, disp=disp)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_set_binding_tensor(h, 0, [0.9 * w0 ** 2] * 3)
+        assert e.value.status == pic.PIC_EDTLIMIT
+    finally:
+        pic.pic_destroy(h)

@@ -28,8 +28,8 @@ MUTATIONS = [
     ("Yee curl sign", "s->B[2][c] -= dt * (tBzx - tBzy);", "s->B[2][c] -= dt * (tBzx + tBzy);",
      "test_yee_plane_waves_follow_numerical_dispersion"),
     ("Hooke force sign",
-     "kick[a] = 0.5 * dt * (q / m * E[a] - omega0[a] * omega0[a] * D[a]);",
-     "kick[a] = 0.5 * dt * (q / m * E[a] + omega0[a] * omega0[a] * D[a]);",
+     "kick[a] = 0.5 * dt * (q / m * E[a] - hooke);",
+     "kick[a] = 0.5 * dt * (q / m * E[a] + hooke);",
      "test_bound_push_reproduces_taflove_recurrence"),
     ("damping sign", "rhs[r] = (1.0 - 0.5 * dt * gamma[r]) * vm[r];",
      "rhs[r] = (1.0 + 0.5 * dt * gamma[r]) * vm[r];", "test_bound_damping_factor"),
