@@ -28,3 +28,13 @@ def test_sqrt_law_on_exact_data():
     assert abs(A - 0.37) < 1e-12 and abs(r2 - 1) < 1e-12
     A, r2 = relax.sqrt_law(t, 0.37 * np.sqrt(t) + 0.05 * np.cos(t))
     assert abs(A - 0.37) < 0.02 and r2 < 1
+
+
+def test_workload_fermi_energy_agrees_with_the_oracle():
+    """The bulk-cube workload's E_F (Sec. 2, exponent 2/3) equals the
+    oracle's pinned Fermi energy for the study's three densities."""
+    from oracle import oracle as O
+    from paper_2501_07465_gb300 import inputs as I
+    for n in (2e28, 4e28, 6e28):
+        wl = I.bulk_cube(n, 32)
+        assert abs(wl["species"][0]["E_F"] / O.fermi_energy(n, I.ME) - 1) < 1e-12
