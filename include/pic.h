@@ -12,10 +12,15 @@
  *                modlorentz), modified Boris push (Appendix A.2);
  *   PIC_DIRAC -- massless Dirac carriers of a sheet in the x-y plane (Sec. 5):
  *                Boris push with the transverse mass, |v| renormalised to v_F.
- * A step gathers E^n and B^n to every particle (CIC), pushes it, reflects
- * free and Dirac particles specularly at the material edges, deposits the
- * current with Esirkepov's charge-conserving scheme and advances the fields
- * with Yee FDTD (CPML layers and a soft plane-wave current sheet optional).
+ * A step gathers E^n and B^n to every particle (CIC, or TSC for free and
+ * Dirac particles: pic_set_shape_order), pushes it, applies the surface rule
+ * at the material edges (specular or diffuse reflection, or open edges, with
+ * an optional work-function barrier: pic_set_particle_bc,
+ * pic_set_work_function, pic_set_external_field), deposits the current with
+ * Esirkepov's charge-conserving scheme and advances the fields with Yee FDTD
+ * (CPML layers, a soft plane-wave current sheet and a per-cell permittivity
+ * optional).  Bound species may carry per-axis damping and a full binding
+ * tensor (pic_set_binding_tensor).
  *
  * Conventions for every call:
  *  - Units are SI.  Cells are indexed x fastest: c = (k*ny + j)*nx + i.
