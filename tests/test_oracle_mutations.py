@@ -93,6 +93,23 @@ MUTATIONS = [
      "test_energy_histogram_bin_edges"),
     ("histogram energy factor", "double E = 0.5 * sp->m * ((v[0] * v[0]",
      "double E = sp->m * ((v[0] * v[0]", "test_energy_histogram_of_the_T0_fermi_sea"),
+    ("Bn half-step factor", "double hdt = 0.5 * s->dt;", "double hdt = s->dt;",
+     "test_gather_B_is_the_integer_step_average_of_the_eigenmode"),
+    ("Bn correction sign", "s->Bn[0][c] = s->B[0][c] - hdt * (dEz_dy - dEy_dz);",
+     "s->Bn[0][c] = s->B[0][c] + hdt * (dEz_dy - dEy_dz);",
+     "test_gather_B_is_the_integer_step_average_of_the_eigenmode"),
+    ("kinetic energy without the weight",
+     "e += 0.5 * sp->m * sp->w * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);",
+     "e += 0.5 * sp->m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);",
+     "test_diag_energies_hand_computed"),
+    ("electric energy factor", "ue += 0.5 * EPS0 * s->E[a][c] * s->E[a][c] * V;",
+     "ue += EPS0 * s->E[a][c] * s->E[a][c] * V;", "test_diag_energies_hand_computed"),
+    ("magnetic energy with mu0 upside down", "ub += 0.5 / mu0() * s->B[a][c] * s->B[a][c] * V;",
+     "ub += 0.5 * mu0() * s->B[a][c] * s->B[a][c] * V;", "test_diag_energies_hand_computed"),
+    ("Dirac carriers pushed with the plasmon mass",
+     "    orc_push_free(v, E, B, q, m, dt);\n    v[2] = 0.0;",
+     "    orc_push_free(v, E, B, q, 2.0 * m, dt);\n    v[2] = 0.0;",
+     "test_sheet_plasmon_frequency"),
 ]
 
 
