@@ -23,26 +23,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIB_DIR, "liboracle_omp.so")
 
 KIND_FREE, KIND_BOUND, KIND_DIRAC = 0, 1, 2
 BC_PERIODIC, BC_PML = 0, 1
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, parallel: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off so that x86 and Arm
-    hosts round identically)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+    hosts round identically).  parallel: the OpenMP build (all host cores),
+    used only to time the oracle; the checks use the serial build."""
+    out = _LIB_OMP if parallel else _LIB
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
     os.makedirs(_LIB_DIR, exist_ok=True)
-    tmp = _LIB + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", *(["-fopenmp"] if parallel else []), _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
 
 
 _lib = None
+_lib_omp = None
 
 
 def lib():
@@ -51,6 +55,20 @@ def lib():
         _lib = C.CDLL(build())
         _declare(_lib)
     return _lib
+
+
+def lib_omp():
+    """The OpenMP build (timing only)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = C.CDLL(build(parallel=True))
+        _declare(_lib_omp)
+    return _lib_omp
+
+
+def threads(parallel: bool = True) -> int:
+    """Threads the oracle's step runs on."""
+    return (lib_omp() if parallel else lib()).orc_threads()
 
 
 _dp = C.POINTER(C.c_double)
@@ -80,6 +98,8 @@ def _declare(L):
     L.orc_add_species.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_double, _dp,
                                   _dp, C.c_double, C.c_long, _dp, _dp, _dp, C.c_int]
     L.orc_step.argtypes = [C.c_void_p, C.c_int]
+    L.orc_threads.restype = C.c_int
+    L.orc_threads.argtypes = []
     L.orc_get_field.argtypes = [C.c_void_p, C.c_int, _dp]
     L.orc_set_field.argtypes = [C.c_void_p, C.c_int, _dp]
     L.orc_get_J.argtypes = [C.c_void_p, C.c_int, _dp]
@@ -228,10 +248,13 @@ class OracleSim:
     grid keys: dims, n (3 ints), d (3 floats, metres; d[2] is the slab depth
     in 2D), dt, bc (3 ints, 0 periodic / 1 PML), pml_cells, pml_R0, pml_order,
     and optionally a plane-wave source: src (bool), inc_axis, pol_axis,
-    src_index, E0, omega, tau (intensity FWHM), t0.
+    src_index, E0, omega, tau (intensity FWHM), t0.  parallel=True runs the
+    step on the OpenMP build (all host cores; only the summation order of J
+    differs from the serial build), for timing.
     """
 
-    def __init__(self, **g):
+    def __init__(self, parallel=False, **g):
+        self._L = lib_omp() if parallel else lib()
         self.dims = int(g["dims"])
         n = list(g["n"]) + [1] * (3 - len(g["n"]))
         if self.dims == 2:
@@ -242,7 +265,7 @@ class OracleSim:
         d = np.array(g["d"], dtype=np.float64)
         bc = np.array(g.get("bc", [0, 0, 0]), dtype=np.int32)
         self.dt = float(g["dt"])
-        self._h = lib().orc_create(
+        self._h = self._L.orc_create(
             self.dims, nn.ctypes.data_as(_ip), d.ctypes.data_as(_dp), self.dt,
             bc.ctypes.data_as(_ip), int(g.get("pml_cells", 0)), float(g.get("pml_R0", 1e-8)),
             int(g.get("pml_order", 3)), int(bool(g.get("src", False))), int(g.get("inc_axis", 0)),
@@ -252,7 +275,7 @@ class OracleSim:
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -264,49 +287,49 @@ class OracleSim:
     def set_mask(self, mask):
         m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
         assert m.size == np.prod(self.shape)
-        lib().orc_set_mask(self._h, m.ctypes.data_as(_u8p))
+        self._L.orc_set_mask(self._h, m.ctypes.data_as(_u8p))
 
     def set_permittivity(self, eps_r):
         """Relative permittivity per cell, [nz][ny][nx] (None: vacuum)."""
         if eps_r is None:
-            lib().orc_set_permittivity(self._h, None)
+            self._L.orc_set_permittivity(self._h, None)
             return
         e = np.ascontiguousarray(eps_r, dtype=np.float64).reshape(-1)
         assert e.size == np.prod(self.shape)
         self._eps = e
-        lib().orc_set_permittivity(self._h, e.ctypes.data_as(_dp))
+        self._L.orc_set_permittivity(self._h, e.ctypes.data_as(_dp))
 
     def set_external_field(self, E):
         """External electrostatic field (Ex, Ey, Ez), each [nz][ny][nx] on the
         E stagger, seen by the particles only (None: remove)."""
         if E is None:
-            lib().orc_set_external_field(self._h, None, None, None)
+            self._L.orc_set_external_field(self._h, None, None, None)
             self._eext = None
             return
         arrs = [np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(self.shape))
                 for c in E]
         self._eext = arrs
-        lib().orc_set_external_field(self._h, *[a.ctypes.data_as(_dp) for a in arrs])
+        self._L.orc_set_external_field(self._h, *[a.ctypes.data_as(_dp) for a in arrs])
 
     def work_function_field(self, W_eV):
         """The work-function barrier field of height W_eV built from the mask
         (returned, not set)."""
         out = [np.zeros(self.shape) for _ in range(3)]
-        lib().orc_work_function_field(self._h, float(W_eV), *[a.ctypes.data_as(_dp) for a in out])
+        self._L.orc_work_function_field(self._h, float(W_eV), *[a.ctypes.data_as(_dp) for a in out])
         return out
 
     def set_binding_offdiag(self, k, w2off):
         """Off-diagonal (xy, xz, yz) entries of bound species k's Omega^2 (s^-2)."""
         a = np.ascontiguousarray(w2off, dtype=np.float64)
         self._off = a
-        lib().orc_set_binding_offdiag(self._h, int(k), a.ctypes.data_as(_dp))
+        self._L.orc_set_binding_offdiag(self._h, int(k), a.ctypes.data_as(_dp))
 
     def set_shape_order(self, order):
         """1 CIC, 2 TSC for the free and Dirac particles (before add_species)."""
-        lib().orc_set_shape_order(self._h, int(order))
+        self._L.orc_set_shape_order(self._h, int(order))
 
     def set_particle_bc(self, open_edges=False, p_diffuse=0.0, seed=0):
-        lib().orc_set_particle_bc(self._h, int(bool(open_edges)), float(p_diffuse), int(seed))
+        self._L.orc_set_particle_bc(self._h, int(bool(open_edges)), float(p_diffuse), int(seed))
 
     def add_species(self, kind, q, m, w, X, V, D=None, omega0=(0, 0, 0), gamma=(0, 0, 0),
                     vF=0.0, bg=0):
@@ -317,65 +340,65 @@ class OracleSim:
         D, pD = _d(np.asarray(D, dtype=np.float64).reshape(-1, 3))
         _, pw = _d(np.asarray(omega0, dtype=np.float64))
         _, pg = _d(np.asarray(gamma, dtype=np.float64))
-        k = lib().orc_add_species(self._h, kind, q, m, w, pw, pg, vF, X.shape[0], pX, pV, pD, bg)
+        k = self._L.orc_add_species(self._h, kind, q, m, w, pw, pg, vF, X.shape[0], pX, pV, pD, bg)
         if k < 0:
             raise RuntimeError("too many species")
         self.nsp += 1
         return k
 
     def step(self, n=1):
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     def field(self, comp):
         """comp 0..2 E, 3..5 B (half step), 6..8 J of the last step, 9..11 B^n
         used by the last gather."""
         out = np.zeros(self.shape)
-        lib().orc_get_field(self._h, comp, out.ctypes.data_as(_dp))
+        self._L.orc_get_field(self._h, comp, out.ctypes.data_as(_dp))
         return out
 
     def set_field(self, comp, arr):
         a, pa = _d(np.asarray(arr, dtype=np.float64).reshape(self.shape))
-        lib().orc_set_field(self._h, comp, pa)
+        self._L.orc_set_field(self._h, comp, pa)
 
     def J(self, comp):
         out = np.zeros(self.shape)
-        lib().orc_get_J(self._h, comp, out.ctypes.data_as(_dp))
+        self._L.orc_get_J(self._h, comp, out.ctypes.data_as(_dp))
         return out
 
     def clear_J(self):
-        lib().orc_clear_J(self._h)
+        self._L.orc_clear_J(self._h)
 
     def species(self, k):
-        n = lib().orc_species_count(self._h, k)
+        n = self._L.orc_species_count(self._h, k)
         X = np.zeros((max(n, 1), 3))
         V = np.zeros((max(n, 1), 3))
         D = np.zeros((max(n, 1), 3))
         nr = C.c_longlong(0)
-        lib().orc_get_species(self._h, k, X.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
+        self._L.orc_get_species(self._h, k, X.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
                               D.ctypes.data_as(_dp), C.byref(nr))
         return X[:n], V[:n], D[:n], int(nr.value)
 
     def cell_counts(self, k):
         out = np.zeros(self.shape, dtype=np.int32)
-        lib().orc_cell_counts(self._h, k, out.ctypes.data_as(_i32p))
+        self._L.orc_cell_counts(self._h, k, out.ctypes.data_as(_i32p))
         return out
 
     def energy_histogram(self, k, e_max, nbins):
         """Kinetic-energy histogram of species k: nbins bins of width
         e_max / nbins, then the count of E >= e_max (uint64, nbins + 1)."""
         out = np.zeros(nbins + 1, dtype=np.uint64)
-        lib().orc_energy_histogram(self._h, k, float(e_max), int(nbins),
+        self._L.orc_energy_histogram(self._h, k, float(e_max), int(nbins),
                                    out.ctypes.data_as(C.POINTER(C.c_uint64)))
         return out
 
     def rho(self):
         out = np.zeros(self.shape)
-        lib().orc_rho(self._h, out.ctypes.data_as(_dp))
+        self._L.orc_rho(self._h, out.ctypes.data_as(_dp))
         return out
 
     def diag(self):
         out = np.zeros(13)
-        lib().orc_diag(self._h, out.ctypes.data_as(_dp))
+        self._L.orc_diag(self._h, out.ctypes.data_as(_dp))
         return {"kinetic": out[:self.nsp].copy(), "field_E": out[8], "field_B": out[9],
                 "gauss_max": out[10], "gauss_rms": out[11], "rho_max": out[12]}
 
@@ -383,10 +406,10 @@ class OracleSim:
         _, pX = _d(np.asarray(X, dtype=np.float64))
         E = np.zeros(3)
         B = np.zeros(3)
-        lib().orc_gather(self._h, pX, E.ctypes.data_as(_dp), B.ctypes.data_as(_dp))
+        self._L.orc_gather(self._h, pX, E.ctypes.data_as(_dp), B.ctypes.data_as(_dp))
         return E, B
 
     def deposit_one(self, X0, X1, qw, vz=0.0):
         _, p0 = _d(np.asarray(X0, dtype=np.float64))
         _, p1 = _d(np.asarray(X1, dtype=np.float64))
-        lib().orc_deposit_one(self._h, p0, p1, qw, vz)
+        self._L.orc_deposit_one(self._h, p0, p1, qw, vz)

@@ -35,6 +35,13 @@
  *      (i+1/2, j, k) and the other components of cell (i, j, k) take the
  *      cell's eps_r).
  *
+ * Threads: compiled with -fopenmp (a separate library used only to time the
+ * oracle on all host cores), the cell loops of steps 1 and 4 and the particle
+ * loop of step 2 run in parallel and the deposit's additions to J are atomic;
+ * the arithmetic of every particle and every cell is unchanged, only the
+ * order in which J's FP64 contributions are summed differs.  The test suite
+ * uses the serial build, where these directives are absent.
+ *
  * Parity pins: every function below is pinned by a CPU test against a closed
  * form, an invariant or a brute-force check (tests/test_oracle_pins.py).  The
  * CPML absorption quality is the one part checked only for decay, not against
@@ -44,6 +51,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* CODATA SI constants (exact c; eps0 from CODATA 2018; mu0 from c and eps0). */
 static const double C_LIGHT = 299792458.0;
@@ -148,6 +158,9 @@ static double fget(const orc_sim *s, const double *F, int i, int j, int k) {
 static void fadd(const orc_sim *s, double *F, int i, int j, int k, double v) {
     int c[3] = {i, j, k};
     if (!wrap_index(s, c)) return; /* deposits beyond a wall are dropped */
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
     F[idx3(s, c[0], c[1], c[2])] += v;
 }
 
@@ -781,6 +794,9 @@ static void compute_Bn(orc_sim *s) {
     const double *dd = s->d;
     double hdt = 0.5 * s->dt;
     int D3 = s->dims == 3;
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
     for (int k = 0; k < s->n[2]; ++k)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
@@ -829,6 +845,9 @@ static void yee_update(orc_sim *s) {
     const double c2 = C_LIGHT * C_LIGHT;
     int D3 = s->dims == 3;
     /* B^{n+1/2} from E^n */
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
     for (int k = 0; k < s->n[2]; ++k)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
@@ -853,6 +872,9 @@ static void yee_update(orc_sim *s) {
                 s->B[2][c] -= dt * (tBzx - tBzy);
             }
     /* E^{n+1} from B^{n+1/2} and J^{n+1/2} */
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static)
+#endif
     for (int k = 0; k < s->n[2]; ++k)
         for (int j = 0; j < s->n[1]; ++j)
             for (int i = 0; i < s->n[0]; ++i) {
@@ -884,6 +906,10 @@ static void yee_update(orc_sim *s) {
 
 static void push_species(orc_sim *s, orc_species *sp, int k) {
     const double dt = s->dt;
+    long long nrefl = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : nrefl)
+#endif
     for (long p = 0; p < sp->n; ++p) {
         double X0[3], X1[3], E[3], B[3];
         double *v = &sp->V[3 * p];
@@ -899,7 +925,7 @@ static void push_species(orc_sim *s, orc_species *sp, int k) {
             if (sp->kind == KIND_FREE) orc_push_free(v, E, B, sp->q, sp->m, dt);
             else orc_push_dirac(v, E, B, sp->q, sp->m, dt, sp->vF);
             for (int a = 0; a < 3; ++a) X1[a] = X0[a] + (a < s->dims ? dt * v[a] / s->d[a] : 0.0);
-            sp->nrefl += reflect(s, sp, k, p, X0, X1, v);
+            nrefl += reflect(s, sp, k, p, X0, X1, v);
         }
         esirkepov(s, order, X0, X1, sp->q * sp->w, v[2]);
         if (sp->kind != KIND_BOUND) {
@@ -914,6 +940,16 @@ static void push_species(orc_sim *s, orc_species *sp, int k) {
             }
         }
     }
+    sp->nrefl += nrefl;
+}
+
+/* threads the step uses (1 in the serial build) */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void orc_step(void *h, int nsteps) {
