@@ -157,7 +157,9 @@ typedef struct pic_tuning {
     int keep_J;         /* 1: J of the last step stays readable (tests) [0] */
     int timing;         /* 1: time every kernel launch with CUDA events [0] */
     int field_plain;    /* 1: field kernel with plain loads even where TMA applies [0] */
-    int tile_order;     /* particles inside a tile: 0 spread over cells, 1 cell order [0] */
+    int tile_order;     /* particles inside a tile: 0 cells interleaved (rank inside the
+                           cell, then cell: a warp's lanes in consecutive cells), 1 arrival
+                           order, 2 spread over the cells by a multiplicative permutation [0] */
     int no_overlap;     /* 0: the field work that does not need this step's current runs
                            beside the particle phase on a second stream of the handle --
                            the B pass (field_mode 2), or the whole fused update with the
@@ -169,6 +171,15 @@ typedef struct pic_tuning {
                            shared memory or barriers); 3: one streaming pass (48 B/cell,
                            no shared memory or barriers: the -x neighbour's B by warp
                            shuffle, the -y one recomputed); 0: keep the current mode [2] */
+    int64_t wait_polls; /* polls after which a TMA-fed field pass stops waiting for a copy
+                           and latches PIC_ETIMEOUT [2^23, about 0.5 s]; copies already in
+                           flight are always waited for in full before a CTA exits.  A
+                           small value makes the waits give up (tests of the timeout path) */
+    int field_overlap;  /* field_mode 2 with overlap: 1 the B pass runs beside the particle
+                           phase, the E pass after it; 2 both passes run beside it (the E
+                           pass without this step's current) and a short pass over the field
+                           blocks the deposit touched then subtracts (dt / eps0) J from
+                           E^{n+1}; 0: keep the current choice [1] */
 } pic_tuning;
 
 /* Results of pic_diagnostics (FP64 reductions on the device). */
@@ -224,8 +235,7 @@ pic_status pic_set_material_mask(pic_sim *sim, const uint8_t *mask, size_t n);
    n = number of cells values [nz][ny][nx], finite, 1e-6 .. 1e6 (else
    PIC_EINVAL; the library keeps its own copy of 1 / eps_r); NULL returns to
    vacuum.  Needs field_mode 2 (PIC_ESTATE otherwise; pic_set_tuning then
-   refuses modes 1 and 3), and such a simulation steps alone (pic_group_add
-   refuses it). */
+   refuses modes 1 and 3); in a group the batched field update applies it. */
 pic_status pic_set_permittivity(pic_sim *sim, const float *eps_r, size_t n);
 
 /* External electrostatic field (Sec. 3, the work-function model): a static
@@ -271,9 +281,9 @@ pic_status pic_set_work_function(pic_sim *sim, double W_eV);
    with pic_set_work_function, the potential-wall surface); p_diffuse must
    be 0.
    Non-periodic domain faces reflect specularly under either rule.  edges
-   outside the enum or p_diffuse outside [0, 1]: PIC_EINVAL.  A simulation
-   with p_diffuse > 0 steps alone (pic_group_add refuses it: a captured
-   group epoch would not advance the draws' step index). */
+   outside the enum or p_diffuse outside [0, 1]: PIC_EINVAL.  In a group the
+   step index of the draws is the member's own (its device step count), so
+   the draws equal those of the simulation stepped alone. */
 pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64_t seed);
 
 /* Shape function W of Sec. 4.1 for the free and Dirac particles: order 1
@@ -283,8 +293,8 @@ pic_status pic_set_particle_bc(pic_sim *sim, int edges, double p_diffuse, uint64
    nodes per axis, and the charge density of the Gauss diagnostic with the
    same shape).  Bound particles keep CIC.  Must precede pic_load_species
    (PIC_ESTATE otherwise: a species' ion background is deposited with its
-   shape); other orders: PIC_EINVAL.  A TSC simulation steps alone
-   (pic_group_add refuses it). */
+   shape); other orders: PIC_EINVAL.  A group's members share one shape
+   order (pic_group_add refuses a member of the other order). */
 pic_status pic_set_shape_order(pic_sim *sim, int order);
 
 /* Full symmetric binding tensor of bound species `species` (Eq. modlorentz
@@ -356,8 +366,10 @@ const char *pic_last_error(const pic_sim *sim);
 /* ------------------------------------------------------------------------
    Batch engine: many independent simulations (for example nanostructures of
    uneven size) advanced by the same launches.
-   A group holds up to `capacity` simulations of one dimensionality and one
-   particle tile size (the first member fixes both).  pic_group_step advances
+   A group holds up to `capacity` simulations of one dimensionality, one
+   particle tile size and one shape order (the first member fixes them; a
+   member may carry a permittivity, a boundary variant of Sec. 3 or an
+   anisotropic bound species).  pic_group_step advances
    every member that has steps left -- a member added with nsteps stops after
    nsteps -- with one persistent launch for the particle phase of all members
    and one launch for their field phase per step; the tile re-sorts of all

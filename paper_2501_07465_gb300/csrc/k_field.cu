@@ -265,9 +265,16 @@ __device__ void field_block(const GridP &g, const FieldP &f, const int blk_x, co
             float tEzx = cpml_term(f, 0, 1, px, i, false, dBy_dx, true);
             float dBx_dy = (bx - sB[0][Y - 1][X]) * g.inv_d[1];
             float tEzy = cpml_term(f, 1, 1, py, j, false, dBx_dy, true);
-            f.En[0][o] = sE[cur][0][Y][X] + f.c2dt * (tExy - tExz) - f.dt_eps0 * jx;
-            f.En[1][o] = sE[cur][1][Y][X] + f.c2dt * (tEyz - tEyx) - f.dt_eps0 * jy;
-            f.En[2][o] = sE[cur][2][Y][X] + f.c2dt * (tEzx - tEzy) - f.dt_eps0 * jz;
+            if (f.inv_eps) {  // eps dE/dt = curl H - J (Eq. consteps), uniform per CTA
+                const float ie = __ldg(f.inv_eps + o);
+                f.En[0][o] = sE[cur][0][Y][X] + ie * (f.c2dt * (tExy - tExz) - f.dt_eps0 * jx);
+                f.En[1][o] = sE[cur][1][Y][X] + ie * (f.c2dt * (tEyz - tEyx) - f.dt_eps0 * jy);
+                f.En[2][o] = sE[cur][2][Y][X] + ie * (f.c2dt * (tEzx - tEzy) - f.dt_eps0 * jz);
+            } else {
+                f.En[0][o] = sE[cur][0][Y][X] + f.c2dt * (tExy - tExz) - f.dt_eps0 * jx;
+                f.En[1][o] = sE[cur][1][Y][X] + f.c2dt * (tEyz - tEyx) - f.dt_eps0 * jy;
+                f.En[2][o] = sE[cur][2][Y][X] + f.c2dt * (tEzx - tEzy) - f.dt_eps0 * jz;
+            }
             Bx_prev = bx;
             By_prev = by;
         }
@@ -312,7 +319,8 @@ __global__ void __launch_bounds__(BX * BY)
 // cleared and the step counter advances.  Same arithmetic as the fused update
 // (E^n + c^2 dt curl B - (dt/eps0) J, one multiply-add per term).
 template <int DIM>
-__global__ void __launch_bounds__(BX * BY) japply_kernel(GridP g, FieldP f, long long *counter) {
+__global__ void __launch_bounds__(BX * BY)
+    japply_kernel(GridP g, FieldP f, const float *inv_eps, long long *counter) {
     const long long b = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
     if (counter && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
         *counter += 1;
@@ -323,9 +331,12 @@ __global__ void __launch_bounds__(BX * BY) japply_kernel(GridP g, FieldP f, long
     if (i < g.n[0] && j < g.n[1]) {
         for (int k = k0; k < k1; ++k) {
             const long long o = ((long long)k * g.n[1] + j) * g.n[0] + i;
+            // eps dE/dt = curl H - J (Eq. consteps): the current's share of
+            // E^{n+1}, 1/eps_r of it where a permittivity is set
+            const float dte = inv_eps ? f.dt_eps0 * __ldg(inv_eps + o) : f.dt_eps0;
             for (int c = 0; c < 3; ++c) {
                 const float jc = f.J[c][o];
-                f.En[c][o] = __fmaf_rn(-f.dt_eps0, jc, f.En[c][o]);
+                f.En[c][o] = __fmaf_rn(-dte, jc, f.En[c][o]);
                 if (!f.keepJ) f.J[c][o] = 0.f;
             }
         }
@@ -344,10 +355,11 @@ cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdesc
     return cudaGetLastError();
 }
 
-cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s) {
+cudaError_t launch_japply(const GridP &g, const FieldP &f, const float *inv_eps, long long *counter,
+                          cudaStream_t s) {
     dim3 grid(f.nbx, f.nby, f.nbz);
-    if (g.dims == 3) japply_kernel<3><<<grid, BX * BY, 0, s>>>(g, f, counter);
-    else japply_kernel<2><<<grid, BX * BY, 0, s>>>(g, f, counter);
+    if (g.dims == 3) japply_kernel<3><<<grid, BX * BY, 0, s>>>(g, f, inv_eps, counter);
+    else japply_kernel<2><<<grid, BX * BY, 0, s>>>(g, f, inv_eps, counter);
     return cudaGetLastError();
 }
 

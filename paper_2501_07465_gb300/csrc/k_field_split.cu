@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(BX * BY)
     __shared__ float s_src;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long long bflag = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
-    const bool jdirty = f.jdirty[bflag] != 0;
+    // splitJ: the pass runs beside the particle phase and leaves J (and the
+    // block flags) to the current pass that follows it
+    const bool jdirty = !f.splitJ && f.jdirty[bflag] != 0;
     float src;
     if (f.src_host || !f.src_on) {
         src = f.src_on ? f.src_val : 0.f;

@@ -40,7 +40,6 @@ constexpr int E_PAD = 1664, B_PAD = 1408, J_PAD = 1024;  // 128-byte aligned com
 constexpr int STAGE = 3 * (E_PAD + B_PAD + J_PAD);
 constexpr int SB_FLOATS = 3 * (BY + 1) * (BX + 1);
 constexpr int SB_BYTES = (SB_FLOATS * 4 + 127) / 128 * 128;
-constexpr long long kWaitIters = 1LL << 23;  // ~0.5 s with the back-off
 
 __device__ inline uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -67,9 +66,27 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; false = gave up
-__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (long long it = 0; it < kWaitIters; ++it) {
+__device__ inline bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false = gave up.  A limit below the default (the tests'
+// knob) polls with the non-blocking test_wait, so that the limit counts
+// polls and not the hardware's own suspension inside try_wait.
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kWaitPolls) {
+    if (limit < kWaitPolls) {
+        for (long long it = 0; it < limit; ++it)
+            if (mbar_test_wait(bar, parity)) return true;
+        return false;
+    }
+    for (long long it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 32) __nanosleep(64);
     }
@@ -656,11 +673,12 @@ __global__ void __launch_bounds__(NT) field_b_kernel_tma(GridP g, FieldP f,
     const int e = (ty + 1) * EW + tx + 4, b = (ty + 1) * BW + tx + 4;
     const long long pl = (long long)nx * ny;
     long long o = ((long long)k0 * ny + j0 + ty) * nx + i0 + tx;
-    bool ok = mbar_wait(&full[0], 0);
+    const long long lim = f.wait_polls;
+    bool ok = mbar_wait(&full[0], 0, lim);
     if (ok) waited = 0;
     for (int p = 0; ok && p < np - 1; ++p, o += pl) {
         const int s = p % SBP, s1 = (p + 1) % SBP;
-        if (!mbar_wait(&full[s1], ((p + 1) / SBP) & 1)) {
+        if (!mbar_wait(&full[s1], ((p + 1) / SBP) & 1, lim)) {
             ok = false;
             break;
         }
@@ -683,7 +701,7 @@ __global__ void __launch_bounds__(NT) field_b_kernel_tma(GridP g, FieldP f,
         // plane p is the last reader of stage s: release it, refill it
         mbar_arrive(&empty[s]);
         if (threadIdx.x == 0 && p + SBP < np) {
-            if (!mbar_wait(&empty[s], (p / SBP) & 1)) {
+            if (!mbar_wait(&empty[s], (p / SBP) & 1, lim)) {
                 ok = false;
                 s_abort = 1;
                 break;

@@ -35,11 +35,9 @@ size_t particle_smem_bytes(const TileP &tp) { return (size_t)9 * tp.boxn * sizeo
 
 template <int DIM>
 cudaError_t particle_setup_dim(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(batch_particle_kernel<DIM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(batch_particle_kernel<DIM>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(particle_kernel<DIM>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_dynamic_smem(particle_kernel<DIM>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM>,
                                                          kThreads, smem);
@@ -58,17 +56,21 @@ cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *
 
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
                                   const int *active, const int2 *items, int nitems, int *sched,
-                                  int nctas, size_t smem, bool ext, cudaStream_t s) {
+                                  const long long *done, int nctas, size_t smem, bool ext,
+                                  int shape, cudaStream_t s) {
+    if (shape == 2)
+        return launch_batch_particles_tsc(dims, descs, fpar, active, items, nitems, sched, done,
+                                          nctas, smem, s);
     if (ext)
-        return launch_batch_particles_ext(dims, descs, fpar, active, items, nitems, sched, nctas,
-                                          smem, s);
+        return launch_batch_particles_ext(dims, descs, fpar, active, items, nitems, sched, done,
+                                          nctas, smem, s);
     if (nctas < 1) nctas = 1;
     if (dims == 3)
         batch_particle_kernel<3><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems,
-                                                               sched);
+                                                               sched, done);
     else
         batch_particle_kernel<2><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items, nitems,
-                                                               sched);
+                                                               sched, done);
     return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@ namespace pic {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kParticleThreads;  // the chunk of the cell-interleaved order
 constexpr int kHalo = 2;  // box covers local cells [-2, T+2]
 
 __device__ inline float clamp_below_one(float f) {
@@ -633,6 +633,100 @@ __device__ inline void deposit_nocross(const Acc &A, const int *c, const float *
     }
 }
 
+// The no-crossing current of a thread's consecutive particles in one cell,
+// summed in registers before it reaches the shared J tile: with the
+// cell-interleaved order a thread meets the particles of a cell in a row, so
+// one flush of (up to) 12 shared atomics serves all of them.  Slots: J_x at
+// the cell's (y, z) corners (0,0) (0,1) (1,0) (1,1); J_y at the (x, z)
+// corners; J_z at the (x, y) corners (2D: the z = 0 corners only).
+struct CellJ {
+    int e;  // box index of the summed cell, -1: none
+    float j[12];
+};
+
+template <int DIM, class Box>
+__device__ inline void cellj_flush(const Box &box, CellJ &a) {
+    if (a.e < 0) return;
+    const int e = a.e, sy = box.b0, sz = box.b01;
+    auto put = [&](int c, int o, float v) {
+        if (v != 0.f) atomicAdd(&box.J[c][e + o], v);
+    };
+    put(0, 0, a.j[0]);
+    put(0, sy, a.j[2]);
+    put(1, 0, a.j[4]);
+    put(1, 1, a.j[6]);
+    put(2, 0, a.j[8]);
+    put(2, sy, a.j[9]);
+    put(2, 1, a.j[10]);
+    put(2, 1 + sy, a.j[11]);
+    if (DIM == 3) {
+        put(0, sz, a.j[1]);
+        put(0, sy + sz, a.j[3]);
+        put(1, sz, a.j[5]);
+        put(1, 1 + sz, a.j[7]);
+    }
+    a.e = -1;
+}
+
+// deposit_nocross into the register sum of the particle's cell (box index
+// of local cell c), flushing the previous cell's sum first.  The same
+// contributions as deposit_nocross, summed in another order.
+template <int DIM, class Box>
+__device__ inline void deposit_nocross_acc(const Box &box, const int *c, const float *f0,
+                                           const float *dF, const float *jf, float vz, CellJ &a) {
+    const int e = box.idx(c[0], c[1], c[2]);
+    if (e != a.e) {
+        cellj_flush<DIM>(box, a);
+        a.e = e;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) a.j[k] = 0.f;
+    }
+    const float k12 = 1.0f / 12.0f;
+    float m0[2], m1[2], m2[2] = {1.f, 0.f};
+    {
+        float fm = f0[0] + 0.5f * dF[0];
+        m0[0] = 1.f - fm;
+        m0[1] = fm;
+        fm = f0[1] + 0.5f * dF[1];
+        m1[0] = 1.f - fm;
+        m1[1] = fm;
+        if (DIM == 3) {
+            fm = f0[2] + 0.5f * dF[2];
+            m2[0] = 1.f - fm;
+            m2[1] = fm;
+        }
+    }
+    if (DIM == 3) {
+        const float cx = -jf[0] * dF[0], ex = dF[1] * dF[2] * k12;
+        a.j[0] += cx * (m1[0] * m2[0] + ex);
+        a.j[1] += cx * (m1[0] * m2[1] - ex);
+        a.j[2] += cx * (m1[1] * m2[0] - ex);
+        a.j[3] += cx * (m1[1] * m2[1] + ex);
+        const float cy = -jf[1] * dF[1], ey = dF[0] * dF[2] * k12;
+        a.j[4] += cy * (m0[0] * m2[0] + ey);
+        a.j[5] += cy * (m0[0] * m2[1] - ey);
+        a.j[6] += cy * (m0[1] * m2[0] - ey);
+        a.j[7] += cy * (m0[1] * m2[1] + ey);
+        const float cz = -jf[2] * dF[2], ez = dF[0] * dF[1] * k12;
+        a.j[8] += cz * (m0[0] * m1[0] + ez);
+        a.j[9] += cz * (m0[0] * m1[1] - ez);
+        a.j[10] += cz * (m0[1] * m1[0] - ez);
+        a.j[11] += cz * (m0[1] * m1[1] + ez);
+    } else {
+        const float cx = -jf[0] * dF[0];
+        a.j[0] += cx * m1[0];
+        a.j[2] += cx * m1[1];
+        const float cy = -jf[1] * dF[1];
+        a.j[4] += cy * m0[0];
+        a.j[6] += cy * m0[1];
+        const float fz = jf[2] * vz, ez = dF[0] * dF[1] * k12;
+        a.j[8] += fz * (m0[0] * m1[0] + ez);
+        a.j[9] += fz * (m0[0] * m1[1] - ez);
+        a.j[10] += fz * (m0[1] * m1[0] - ez);
+        a.j[11] += fz * (m0[1] * m1[1] + ez);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // one particle
 // ---------------------------------------------------------------------------
@@ -705,10 +799,11 @@ __device__ inline void diffuse_velocity(float *v, int ax, int sgn, float u1, flo
 }
 
 // Free electrons and Dirac carriers (species index si), shape order S.
-template <int DIM, int KIND, bool X, int S = 1, class Box = BoxAcc>
+// ACC: a fast no-crossing move's current goes to the register sum acc.
+template <int DIM, int KIND, bool X, int S = 1, bool ACC = false, class Box = BoxAcc>
 __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &s, int si,
                                        long long p, const int *org, const Box &box,
-                                       const GlobalAcc<DIM, X> &glob) {
+                                       const GlobalAcc<DIM, X> &glob, CellJ &acc) {
     const GridP &g = P.g;
     const uint32_t pc = s.cell[p];
     const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
@@ -793,7 +888,8 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
     } else if (!(sh[0] | sh[1] | sh[2])) {
         // stays in its cell: f1 - f0 is exact in FP32 (Sterbenz)
         const float dF[3] = {f1[0] - f0[0], f1[1] - f0[1], DIM == 3 ? f1[2] - f0[2] : 0.f};
-        if (fast) deposit_nocross<DIM>(box, lc, f0, dF, s.jfac, v[2]);
+        if (fast && ACC) deposit_nocross_acc<DIM>(box, lc, f0, dF, s.jfac, v[2], acc);
+        else if (fast) deposit_nocross<DIM>(box, lc, f0, dF, s.jfac, v[2]);
         else deposit_nocross<DIM>(glob, gc, f0, dF, s.jfac, v[2]);
     } else {
         int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
@@ -824,10 +920,10 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
 // directly: it is far below an FP32 ulp of the offset, and the displacement D
 // itself is ~100x the per-step move, so differences of stored values would
 // lose most of its bits.
-template <int DIM, bool X, class Box = BoxAcc>
+template <int DIM, bool X, bool ACC = false, class Box = BoxAcc>
 __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, long long p,
                                   const int *org, const Box &box,
-                                  const GlobalAcc<DIM, X> &glob) {
+                                  const GlobalAcc<DIM, X> &glob, CellJ &acc) {
     const GridP &g = P.g;
     const uint32_t pc = s.cell[p];
     const int gc[3] = {cell_x(pc), cell_y(pc), DIM == 3 ? cell_z(pc) : 0};
@@ -868,7 +964,8 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, lo
         // more than one cell in one step (or NaN): record, deposit nothing
         atomicOr(P.status, kStatusBounds);
     } else if (!(sh[0] | sh[1] | sh[2])) {
-        if (fast) deposit_nocross<DIM>(box, c0, f0, dF, s.jfac, v[2]);
+        if (fast && ACC) deposit_nocross_acc<DIM>(box, c0, f0, dF, s.jfac, v[2], acc);
+        else if (fast) deposit_nocross<DIM>(box, c0, f0, dF, s.jfac, v[2]);
         else {
             int g0[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
             deposit_nocross<DIM>(glob, g0, f0, dF, s.jfac, v[2]);
@@ -938,11 +1035,31 @@ struct BoxWalk {
     }
 };
 
+// Hint that particle p of species s will be read soon: its SoA words are
+// pulled into L2 while the thread works on the particle before it.
+template <int KIND>
+__device__ inline void prefetch_particle(const SpeciesP &s, long long p) {
+    auto pf = [](const void *q) { asm volatile("prefetch.global.L2 [%0];" ::"l"(q)); };
+    pf(s.cell + p);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        pf(s.v[a] + p);
+        if (KIND == PIC_BOUND) {
+            pf(s.anchor32[a] + p);
+            pf(s.disp[a] + p);
+        } else {
+            pf(s.o[a] + p);
+        }
+    }
+}
+
 // One tile of one simulation: stage the field box, push every particle of
 // the tile (all species), flush the J box.  P must live in parameter or shared
 // memory (not global), so that the compiler keeps its fields in registers
 // across the particle stores.
-template <int DIM, bool X, int S = 1>
+// ACC: sum each thread's no-crossing current per cell in registers (the
+// particles are in the cell-interleaved order).
+template <int DIM, bool X, int S = 1, bool ACC = false>
 __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, unsigned *s_refl) {
     constexpr int H = S == 2 ? 3 : kHalo;  // box halo (cells)
     const TileP &tp = P.tp;
@@ -1034,22 +1151,33 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
         }
         __syncthreads();
     }
+    CellJ acc;
+    acc.e = -1;
     for (int si = 0; si < P.nsp; ++si) {
         const SpeciesP &s = P.sp[si];
         const long long a = s.tile_start[t], b = s.tile_start[t + 1];
         unsigned r = 0;
+        // ACC kernels hint the thread's next particle into L2
+        const long long nb = ACC ? (long long)blockDim.x : 0;
         if (s.kind == PIC_BOUND) {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                push_bound<DIM, X>(P, s, p, org, box, glob);
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
+                if (ACC && p + nb < b) prefetch_particle<PIC_BOUND>(s, p + nb);
+                push_bound<DIM, X, ACC>(P, s, p, org, box, glob, acc);
+            }
         } else if (s.kind == PIC_DIRAC) {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                r += push_mobile<DIM, PIC_DIRAC, X, S>(P, s, si, p, org, box, glob);
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
+                if (ACC && p + nb < b) prefetch_particle<PIC_DIRAC>(s, p + nb);
+                r += push_mobile<DIM, PIC_DIRAC, X, S, ACC>(P, s, si, p, org, box, glob, acc);
+            }
         } else {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x)
-                r += push_mobile<DIM, PIC_FREE, X, S>(P, s, si, p, org, box, glob);
+            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
+                if (ACC && p + nb < b) prefetch_particle<PIC_FREE>(s, p + nb);
+                r += push_mobile<DIM, PIC_FREE, X, S, ACC>(P, s, si, p, org, box, glob, acc);
+            }
         }
         if (r) atomicAdd(&s_refl[si], r);
     }
+    if (ACC) cellj_flush<DIM>(box, acc);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     // flush the J box; mark the field blocks that received current (lanes of
@@ -1081,7 +1209,7 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
 }
 
 // One particle phase: the persistent CTAs take tiles from the active list.
-template <int DIM, bool X, int S = 1>
+template <int DIM, bool X, int S = 1, bool ACC = false>
 __device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
@@ -1097,7 +1225,7 @@ __device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
         __syncthreads();
         const int it = s_next;
         if (it >= nact) break;
-        tile_pass<DIM, X, S>(P, P.active[it], smem, s_refl);
+        tile_pass<DIM, X, S, ACC>(P, P.active[it], smem, s_refl);
     }
     __syncthreads();
     if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
@@ -1113,9 +1241,14 @@ __device__ __forceinline__ void particle_phase(const ParticleLaunch &P) {
     }
 }
 
+// Resident CTAs per SM the plain kernel's registers are sized for.
+#ifndef PIC_PARTICLE_MINBLOCKS
+#define PIC_PARTICLE_MINBLOCKS 3
+#endif
+
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) particle_kernel(ParticleLaunch P) {
-    particle_phase<DIM, false>(P);
+__global__ void __launch_bounds__(kThreads, PIC_PARTICLE_MINBLOCKS) particle_kernel(ParticleLaunch P) {
+    particle_phase<DIM, false, 1, true>(P);
 }
 
 // The kernel with the boundary variants is held to the plain kernel's 64
@@ -1130,12 +1263,17 @@ __global__ void __launch_bounds__(kThreads, 4) particle_kernel_ext(ParticleLaunc
 // Many simulations in one persistent launch: items[i] = (simulation, tile),
 // tile < 0 = padding.  Each simulation's parameter block (two variants, one
 // per field ping-pong parity) is copied to shared memory for its items.
-// X: the variant with the external field and the anisotropic bound push
-// (k_particle_ext.cu), launched when a member has either.
-template <int DIM, bool X = false>
+// X: the variant with the external field, diffuse reflection and the
+// anisotropic bound push (k_particle_ext.cu), launched when a member has one
+// of them; S = 2: TSC members (k_particle_tsc.cu).  The diffuse draws are
+// keyed on the step index: a member's block holds the index of its first
+// group step in rng_step, and the member's device step count done[] (set
+// by the step's begin pass) is added here, so a captured epoch draws afresh
+// at every step.
+template <int DIM, bool X = false, int S = 1>
 __global__ void __launch_bounds__(kThreads)
     batch_particle_kernel(const ParticleLaunch *descs, const int *fpar, const int *active,
-                          const int2 *items, int nitems, int *sched) {
+                          const int2 *items, int nitems, int *sched, const long long *done) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
     __shared__ ParticleLaunch sP;
@@ -1150,7 +1288,8 @@ __global__ void __launch_bounds__(kThreads)
         if (it >= nitems) break;
         const int2 w = items[it];
         if (w.y < 0 || !active[w.x]) continue;  // uniform over the CTA
-        if (s_sim != w.x) {
+        const bool fresh = s_sim != w.x;
+        if (fresh) {
             const int *src = reinterpret_cast<const int *>(descs + 2 * w.x + fpar[w.x]);
             int *dst = reinterpret_cast<int *>(&sP);
             for (int q = threadIdx.x; q < (int)(sizeof(ParticleLaunch) / 4); q += blockDim.x)
@@ -1158,8 +1297,11 @@ __global__ void __launch_bounds__(kThreads)
         }
         if (threadIdx.x < kMaxSpecies) s_refl[threadIdx.x] = 0;
         __syncthreads();
-        if (threadIdx.x == 0) s_sim = w.x;
-        tile_pass<DIM, X>(sP, w.y, smem, s_refl);
+        if (threadIdx.x == 0) {
+            if (fresh) sP.rng_step += (uint32_t)done[w.x];
+            s_sim = w.x;
+        }
+        tile_pass<DIM, X, S>(sP, w.y, smem, s_refl);
         __syncthreads();
         if (threadIdx.x < sP.nsp && s_refl[threadIdx.x])
             atomicAdd(sP.sp[threadIdx.x].nrefl, (unsigned long long)s_refl[threadIdx.x]);
@@ -1180,11 +1322,17 @@ __global__ void __launch_bounds__(kThreads)
 cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm);
 cudaError_t launch_particles_ext(const ParticleLaunch &pl, int nctas, size_t smem,
                                  cudaStream_t s);
-// the batch kernel with the external field and the anisotropic bound push
+// the batch kernel with the boundary variants and the anisotropic bound push
 // (k_particle_ext.cu)
 cudaError_t launch_batch_particles_ext(int dims, const ParticleLaunch *descs, const int *fpar,
                                        const int *active, const int2 *items, int nitems,
-                                       int *sched, int nctas, size_t smem, cudaStream_t s);
+                                       int *sched, const long long *done, int nctas, size_t smem,
+                                       cudaStream_t s);
+// the batch kernel of TSC members (k_particle_tsc.cu)
+cudaError_t launch_batch_particles_tsc(int dims, const ParticleLaunch *descs, const int *fpar,
+                                       const int *active, const int2 *items, int nitems,
+                                       int *sched, const long long *done, int nctas, size_t smem,
+                                       cudaStream_t s);
 // the TSC kernels (k_particle_tsc.cu), boundary variants included
 cudaError_t particle_tsc_setup(int dims, size_t smem, int *ctas_per_sm);
 cudaError_t launch_particles_tsc(const ParticleLaunch &pl, int nctas, size_t smem,

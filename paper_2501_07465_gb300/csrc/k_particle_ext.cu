@@ -10,11 +10,9 @@ namespace {
 
 template <int DIM>
 cudaError_t ext_setup_dim(size_t smem, int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(particle_kernel_ext<DIM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(particle_kernel_ext<DIM>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(batch_particle_kernel<DIM, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_dynamic_smem(batch_particle_kernel<DIM, true>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel_ext<DIM>,
                                                          kThreads, smem);
@@ -28,14 +26,15 @@ cudaError_t particle_ext_setup(int dims, size_t smem, int *ctas_per_sm) {
 
 cudaError_t launch_batch_particles_ext(int dims, const ParticleLaunch *descs, const int *fpar,
                                        const int *active, const int2 *items, int nitems,
-                                       int *sched, int nctas, size_t smem, cudaStream_t s) {
+                                       int *sched, const long long *done, int nctas, size_t smem,
+                                       cudaStream_t s) {
     if (nctas < 1) nctas = 1;
     if (dims == 3)
         batch_particle_kernel<3, true><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items,
-                                                                     nitems, sched);
+                                                                     nitems, sched, done);
     else
         batch_particle_kernel<2, true><<<nctas, kThreads, smem, s>>>(descs, fpar, active, items,
-                                                                     nitems, sched);
+                                                                     nitems, sched, done);
     return cudaGetLastError();
 }
 

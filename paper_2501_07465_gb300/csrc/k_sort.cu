@@ -136,6 +136,132 @@ __global__ void tile_scatter_kernel(TileP tp, SpeciesP src, const uint32_t *pid_
     }
 }
 
+// Cell-interleaved order inside a tile.  The tile's cells (x fastest) are
+// cut into chunks of `chunk` consecutive cells -- the particle kernel's CTA
+// width -- and each chunk's particles are arranged by their rank inside
+// their cell first and by their cell second.  The lanes of a warp then sit
+// in consecutive cells (the gather's shared loads spread over the banks),
+// and a thread of the particle kernel, which takes every chunk-th particle,
+// meets the particles of one cell in a row (its current can be summed in
+// registers before it goes to the shared J tile).  Inside chunk h the
+// particle of rank r in cell c goes to
+//   (particles of the chunks before h) + sum_{r' < r} N_{h,r'}
+//     + #{c' in h, c' < c : count(c') > r},
+// N_{h,r'} the number of cells of h with more than r' particles.  One CTA
+// per tile; src holds each tile's particles contiguously (from the tile
+// scatter), dst receives them in the same range.  A tile whose fullest cell
+// holds more than rmax particles is written in plain cell order (rank inside
+// the cell last) instead.
+__device__ inline int local_cell_index(const TileP &tp, int t, uint32_t c) {
+    const int tx = t % tp.nt[0], ty = (t / tp.nt[0]) % tp.nt[1], tz = t / (tp.nt[0] * tp.nt[1]);
+    const int lx = cell_x(c) - tx * tp.T[0], ly = cell_y(c) - ty * tp.T[1];
+    const int lz = cell_z(c) - tz * tp.T[2];
+    return (lz * tp.T[1] + ly) * tp.T[0] + lx;
+}
+
+// exclusive scan over the ncl cells of (count > r), or of the counts
+// themselves for r < 0, each thread owning a run of consecutive cells;
+// out[ncl] = the total (scratch: 32 ints)
+__device__ inline void block_scan_cells(const int *cnt, int r, int ncl, int *out, int *wsum) {
+    const int per = (ncl + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(threadIdx.x * per, ncl), c1 = min(c0 + per, ncl);
+    auto val = [&](int c) { return r < 0 ? cnt[c] : (int)(cnt[c] > r); };
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += val(c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = (w > 0 ? wsum[w - 1] : 0) + x - sum;
+    for (int c = c0; c < c1; ++c) {
+        out[c] = run;
+        run += val(c);
+    }
+    if (threadIdx.x == blockDim.x - 1) out[ncl] = wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();  // wsum is reused by the next scan
+}
+
+__global__ void tile_interleave_kernel(TileP tp, SpeciesP src, const uint32_t *pid_src,
+                                       SpeciesP dst, uint32_t *pid_dst, const int *start,
+                                       int *rank, int rmax, int chunk) {
+    extern __shared__ int sm[];
+    __shared__ int wsum[32];
+    __shared__ int s_R;
+    const int t = blockIdx.x;
+    const int a = start[t], b = start[t + 1];
+    if (a == b) return;
+    const int ncl = tp.T[0] * tp.T[1] * tp.T[2];
+    const int nch = (ncl + chunk - 1) / chunk;
+    int *cnt = sm;                          // [ncl]
+    int *cs = cnt + ncl;                    // [ncl + 1]: particles in the cells before c
+    int *pre = cs + ncl + 1;                // [nch][rmax + 1]: ranks below r of chunk h
+    int *tab = pre + nch * (rmax + 1);      // [rmax][ncl + 1]: cells before c holding more than r
+    for (int c = threadIdx.x; c < ncl; c += blockDim.x) cnt[c] = 0;
+    if (threadIdx.x == 0) s_R = 0;
+    __syncthreads();
+    for (int i = a + threadIdx.x; i < b; i += blockDim.x)
+        rank[i] = atomicAdd(&cnt[local_cell_index(tp, t, src.cell[i])], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncl; c += blockDim.x) atomicMax(&s_R, cnt[c]);
+    __syncthreads();
+    const int R = s_R;
+    const bool interleave = R <= rmax;
+    block_scan_cells(cnt, -1, ncl, cs, wsum);
+    if (interleave) {
+        for (int r = 0; r < R; ++r)
+            block_scan_cells(cnt, r, ncl, tab + (size_t)r * (ncl + 1), wsum);
+        for (int h = threadIdx.x; h < nch; h += blockDim.x) {
+            const int lo = h * chunk, hi = min(lo + chunk, ncl);
+            int acc = 0;
+            for (int r = 0; r < R; ++r) {
+                pre[h * (rmax + 1) + r] = acc;
+                const int *row = tab + (size_t)r * (ncl + 1);
+                acc += row[hi] - row[lo];
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+        const uint32_t c = src.cell[i];
+        const int lc = local_cell_index(tp, t, c);
+        const int r = rank[i];
+        long long pos;
+        if (interleave) {
+            const int h = lc / chunk, lo = h * chunk;
+            const int *row = tab + (size_t)r * (ncl + 1);
+            pos = cs[lo] + pre[h * (rmax + 1) + r] + row[lc] - row[lo];
+        } else {
+            pos = cs[lc] + r;
+        }
+        const long long d = a + pos;
+        dst.cell[d] = c;
+        pid_dst[d] = pid_src[i];
+        for (int q = 0; q < 3; ++q) mv(dst.v[q], src.v[q], d, (long long)i);
+        if (src.kind == PIC_BOUND) {
+            for (int q = 0; q < 3; ++q) {
+                mv(const_cast<double *>(dst.anchor[q]), src.anchor[q], d, (long long)i);
+                mv(const_cast<float *>(dst.anchor32[q]), src.anchor32[q], d, (long long)i);
+                mv(dst.disp[q], src.disp[q], d, (long long)i);
+            }
+        } else {
+            for (int q = 0; q < 3; ++q) mv(dst.o[q], src.o[q], d, (long long)i);
+        }
+    }
+}
+
 // The active-tile list goes to the particle kernel, whose persistent CTAs
 // take tiles from it in order as they become free: listing the tiles by
 // descending particle count (largest first) evens out the CTAs' loads.  The
@@ -264,6 +390,36 @@ cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP 
     if (src.n <= 0) return cudaSuccess;
     tile_scatter_kernel<<<grid_for(src.n, 256), 256, 0, s>>>(tp, src, pid_src, dst, pid_dst, start,
                                                              rank, spread ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// Shared memory of the interleave kernel: cell counts, their scan, the
+// per-chunk rank offsets and the per-rank scans, for cell counts up to rmax,
+// within 96 KB.
+static int interleave_rmax(int ncl, int chunk) {
+    const long long budget = 96 * 1024 / 4;
+    const long long nch = (ncl + chunk - 1) / chunk;
+    const long long r = (budget - 2LL * ncl - 1 - nch) / (ncl + 1 + nch);
+    return (int)std::max<long long>(0, std::min<long long>(r, 255));
+}
+
+static size_t interleave_smem(int ncl, int chunk, int rmax) {
+    const long long nch = (ncl + chunk - 1) / chunk;
+    return (size_t)(2LL * ncl + 1 + nch * (rmax + 1) + (long long)rmax * (ncl + 1)) * sizeof(int);
+}
+
+cudaError_t launch_tile_interleave(const TileP &tp, const SpeciesP &src, const uint32_t *pid_src,
+                                   SpeciesP &dst, uint32_t *pid_dst, const int *start, int *rank,
+                                   int chunk, cudaStream_t s) {
+    if (src.n <= 0) return cudaSuccess;
+    const int ncl = tp.T[0] * tp.T[1] * tp.T[2];
+    const int rmax = interleave_rmax(ncl, chunk);
+    const size_t smem = interleave_smem(ncl, chunk, rmax);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;  // tile too large to reorder
+    cudaError_t e = allow_max_dynamic_smem(tile_interleave_kernel);
+    if (e != cudaSuccess) return e;
+    tile_interleave_kernel<<<tp.ntiles, 256, smem, s>>>(tp, src, pid_src, dst, pid_dst, start, rank,
+                                                        rmax, chunk);
     return cudaGetLastError();
 }
 

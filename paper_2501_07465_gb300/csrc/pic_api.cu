@@ -132,8 +132,11 @@ pic_status setup_tiles(pic_sim *s) {
     CK(s, particle_kernel_setup(dims, s->psmem, &per_sm, &per_sm_ext, &per_sm_tsc));
     if (per_sm < 1 || per_sm_ext < 1 || per_sm_tsc < 1)
         return fail(s, PIC_EINVAL, "particle tile does not fit on an SM");
-    // beside the field work, one CTA per SM fewer leaves it room (3 of 4 measured best)
-    const int use_sm = (!s->tun.no_overlap && per_sm > 1) ? per_sm - 1 : per_sm;
+    // beside the field work, one CTA per SM fewer leaves it room when the
+    // kernel fits four (3 of 4 measured best); the plain kernel at three
+    // CTAs per SM keeps all three (2 of 3 measured slower: 0.536 against
+    // 0.496 ms per step on the 256^3 sphere)
+    const int use_sm = (!s->tun.no_overlap && per_sm > 3) ? per_sm - 1 : per_sm;
     const int use_sm_ext = (!s->tun.no_overlap && per_sm_ext > 1) ? per_sm_ext - 1 : per_sm_ext;
     s->particle_ctas = s->tun.particle_ctas > 0 ? s->tun.particle_ctas : use_sm * s->num_sms;
     s->particle_ctas_ext =
@@ -222,8 +225,15 @@ pic_status sort_species(pic_sim *s, int i) {
     CK(s, launch_tile_histogram(s->g, tp, src.cell, sp.n, s->sort_count, s->sort_rank, s->stream));
     CK(s, launch_scan_int(s->sort_count, sp.tile_start, tp.ntiles, s->scan_tmp, 0, s->stream));
     CK(s, launch_tile_scatter(s->g, tp, src, sp.pid[sp.cur], dst, sp.pid[1 - sp.cur],
-                              sp.tile_start, s->sort_rank, s->tun.tile_order == 0, s->stream));
+                              sp.tile_start, s->sort_rank, s->tun.tile_order == 2, s->stream));
     s->launches += 2 + scan_kernel_count(tp.ntiles);
+    if (s->tun.tile_order == 0) {
+        // cell-interleaved order inside each tile, back into the first buffer
+        CK(s, launch_tile_interleave(tp, dst, sp.pid[1 - sp.cur], src, sp.pid[sp.cur],
+                                     sp.tile_start, s->sort_rank, kParticleThreads, s->stream));
+        s->launches += 1;
+        return PIC_OK;
+    }
     sp.cur = 1 - sp.cur;
     return PIC_OK;
 }
@@ -306,6 +316,8 @@ FieldP field_params(pic_sim *s) {
     f.nbz = s->nbz;
     // the split B pass feeds its interior blocks by TMA where the maps exist
     f.tma_b = (s->tun.field_mode == 2 && s->use_tma && !s->tun.field_plain && s->g.dims == 3) ? 1 : 0;
+    f.wait_polls = s->tun.wait_polls > 0 ? s->tun.wait_polls : kWaitPolls;
+    f.inv_eps = s->inv_eps;
     return f;
 }
 
@@ -443,6 +455,7 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
     s->tun.tile[2] = d.dims == 3 ? 4 : 1;
     s->tun.sort_interval = 32;
     s->tun.field_mode = 2;
+    s->tun.field_overlap = 1;
     s->tun.field_zchunk = 16;
     const long long nc = g.ncell;
     bool ok = true;
@@ -643,6 +656,8 @@ pic_status pic_set_binding_tensor(pic_sim *s, int k, const double *w2off) {
         return fail(s, PIC_EDTLIMIT, "dt exceeds the stability limit of Eq. dtlimit with this tensor");
     for (int a = 0; a < 3; ++a) s->sp[k].w2off[a] = w2off[a];
     s->sp[k].has_off = true;
+    // later species are checked against the tensor's bound too
+    s->omega_b2 = std::max(s->omega_b2, lam);
     return PIC_OK;
 }
 
@@ -686,6 +701,11 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     nt.tile_order = t->tile_order;
     nt.no_overlap = t->no_overlap;
     if (t->field_mode >= 1 && t->field_mode <= 3) nt.field_mode = t->field_mode;
+    if (t->wait_polls < 0) return fail(s, PIC_EINVAL, "wait_polls must be >= 0");
+    nt.wait_polls = t->wait_polls;
+    if (t->field_overlap < 0 || t->field_overlap > 2)
+        return fail(s, PIC_EINVAL, "field_overlap must be 0, 1 or 2");
+    if (t->field_overlap > 0) nt.field_overlap = t->field_overlap;
     if (t->field_zchunk > 0 && t->field_zchunk != s->tun.field_zchunk) {
         nt.field_zchunk = t->field_zchunk;
         s->nbz = s->g.dims == 3 ? (s->g.n[2] + nt.field_zchunk - 1) / nt.field_zchunk : 1;
@@ -934,7 +954,30 @@ pic_status pic_step(pic_sim *s, int nsteps) {
                                 sin(f.src_omega * t));
             f.src_host = 1;
         }
-        if (s->tun.field_mode == 2) {
+        if (s->tun.field_mode == 2 && !s->tun.no_overlap && s->tun.field_overlap == 2) {
+            // both passes beside the particle phase: the E pass takes
+            // B^{n+1/2} from the B pass before it and leaves the current (and
+            // the block flags) to the current pass after the join, which also
+            // advances the step counter
+            P.step_counter = nullptr;
+            f.splitJ = 1;
+            CK(s, cudaEventRecord(s->ev_fork, s->stream));
+            record(s, 0, true);
+            CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
+            record(s, 0, false);
+            CK(s, cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+            record(s, 3, true, s->aux);
+            CK(s, launch_field_b_tma(s->g, f, s->maps, s->fcur, s->status, s->aux));
+            CK(s, launch_field_b(s->g, f, s->aux));
+            record(s, 3, false, s->aux);
+            record(s, 1, true, s->aux);
+            CK(s, launch_field_e(s->g, f, s->inv_eps, s->aux));
+            record(s, 1, false, s->aux);
+            CK(s, cudaEventRecord(s->ev_join, s->aux));
+            CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+            CK(s, launch_japply(s->g, f, s->inv_eps, s->step_counter, s->stream));
+            s->launches += 2 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) + (f.tma_b ? 1 : 0);
+        } else if (s->tun.field_mode == 2) {
             // two streaming passes; the B pass reads only E^n, B^{n-1/2} and
             // writes the other ping-pong half, so with overlap it runs beside
             // the particle phase
@@ -983,7 +1026,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             record(s, 1, false, s->aux);
             CK(s, cudaEventRecord(s->ev_join, s->aux));
             CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
-            CK(s, launch_japply(s->g, f, s->step_counter, s->stream));
+            CK(s, launch_japply(s->g, f, s->inv_eps, s->step_counter, s->stream));
             s->launches += 2 + (stream ? fl : 1);
         } else {
             record(s, 0, true);
@@ -1230,6 +1273,9 @@ int *g_noalloc_ptr[kNoallocMaxDevices] = {};
 }  // namespace
 
 extern "C" pic_status pic_cell_counts_noalloc(pic_sim *s, int k, int32_t *out, size_t n) {
+    // a group member's particles move on the group's stream: wait for it, as
+    // every other reader does
+    if (s && s->group_stream) CK(s, cudaStreamSynchronize(s->group_stream));
     if (!s || !out) return fail(s, PIC_EINVAL, "null argument");
     if (k < 0 || k >= s->nsp) return fail(s, PIC_EINVAL, "no such species");
     if ((long long)n != s->g.ncell) return fail(s, PIC_EINVAL, "n must equal the cell count");
@@ -1237,8 +1283,14 @@ extern "C" pic_status pic_cell_counts_noalloc(pic_sim *s, int k, int32_t *out, s
         return fail(s, PIC_EINVAL,
                     "grid has " + std::to_string(n) + " cells; pic_cell_counts_noalloc holds at most " +
                         std::to_string(PIC_NOALLOC_MAX_CELLS) + " (use pic_cell_counts)");
-    int dev = 0;
-    CK(s, cudaGetDevice(&dev));
+    // the array's address is looked up on the simulation's own device, which
+    // must be the current one (the stream and the kernel run there)
+    const int dev = s->device;
+    int cur = -1;
+    CK(s, cudaGetDevice(&cur));
+    if (cur != dev)
+        return fail(s, PIC_EINVAL, "current device " + std::to_string(cur) +
+                                       " is not the simulation's device " + std::to_string(dev));
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(s, PIC_EINVAL, "device index too large");
     int *counts = nullptr;
     {

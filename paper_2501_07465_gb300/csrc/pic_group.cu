@@ -28,7 +28,8 @@ struct pic_group {
     int sort_interval = 32;
     size_t psmem = 0;
     int pctas = 1;
-    bool ext = false;  // some member has an external field or anisotropic gamma
+    bool ext = false;  // some member has a boundary variant or anisotropic gamma
+    int shape = 0;     // the members' shape order (1 CIC, 2 TSC); 0 before the first
     std::vector<pic_sim *> slots;
     std::vector<long long> done, target;  // host mirrors
     bool dirty = true;
@@ -139,6 +140,9 @@ pic_status rebuild(pic_group *g) {
             s->fcur = par;
             hp[2 * k + par] = pic::particle_params(s);
             hp[2 * k + par].step_counter = nullptr;  // begin_step sets the counter
+            // the step index of the member's first group step: the kernel adds
+            // the member's device step count (the diffuse draws' key)
+            hp[2 * k + par].rng_step = (uint32_t)(s->steps - g->done[k]);
             ext = ext || pic::particle_launch_ext(hp[2 * k + par]);
             hf[2 * k + par] = pic::field_params(s);
         }
@@ -255,8 +259,8 @@ pic_status enqueue_step(pic_group *g) {
     GCK(g, pic::launch_begin_step(g->capacity, g->member, g->active, g->fpar, g->ddone, g->dtarget,
                                   g->counters, g->stream));
     GCK(g, pic::launch_batch_particles(g->dims, g->pdesc, g->fpar, g->active, g->pitems,
-                                       g->npitems, g->psched, g->pctas, g->psmem, g->ext,
-                                       g->stream));
+                                       g->npitems, g->psched, g->ddone, g->pctas, g->psmem,
+                                       g->ext, g->shape, g->stream));
     GCK(g, pic::launch_batch_field(g->dims, g->grids, g->fdesc, g->fpar, g->active, g->fitems,
                                    g->nfitems, g->stream));
     g->launches += 3;
@@ -319,24 +323,19 @@ pic_status pic_group_add(pic_group *g, pic_sim *s, int64_t nsteps) {
     if (!g || !s) return gfail(g, PIC_EINVAL, "null argument");
     if (s->group) return gfail(g, PIC_ESTATE, "simulation already belongs to a group");
     if (nsteps < 0) return gfail(g, PIC_EINVAL, "nsteps must be >= 0");
-    if (s->inv_eps)
-        return gfail(g, PIC_EINVAL, "a simulation with a permittivity steps alone (pic_step)");
-    // the diffuse draws take the step index from the host, which a captured
-    // epoch does not update
-    if (s->p_diffuse > 0.0)
-        return gfail(g, PIC_EINVAL, "a simulation with diffuse reflection steps alone");
-    if (s->shape_order != 1)
-        return gfail(g, PIC_EINVAL, "a simulation with TSC shapes steps alone");
     if (g->dims == 0) {
         g->dims = s->g.dims;
         for (int a = 0; a < 3; ++a) g->tile[a] = s->tp.T[a];
         g->sort_interval = std::max(1, s->tun.sort_interval);
-        g->psmem = s->psmem;
-        int per_sm = 0, per_sm_ext = 0;
-        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm, &per_sm_ext));
-        g->pctas = std::max(1, per_sm) * s->num_sms;
+        g->shape = s->shape_order;
+        g->psmem = s->psmem;  // the staged box of the shape (TSC: one cell more a side)
+        int per_sm = 0, per_sm_ext = 0, per_sm_tsc = 0;
+        GCK(g, pic::particle_kernel_setup(g->dims, g->psmem, &per_sm, &per_sm_ext, &per_sm_tsc));
+        g->pctas = std::max(1, g->shape == 2 ? per_sm_tsc : per_sm) * s->num_sms;
     }
     if (s->g.dims != g->dims) return gfail(g, PIC_EINVAL, "members must share dims");
+    if (s->shape_order != g->shape)
+        return gfail(g, PIC_EINVAL, "members must share the shape order (CIC or TSC)");
     for (int a = 0; a < 3; ++a)
         if (s->tp.T[a] != g->tile[a]) return gfail(g, PIC_EINVAL, "members must share the particle tile");
     if (g->budget && member_bytes(g) + s->bytes > g->budget)

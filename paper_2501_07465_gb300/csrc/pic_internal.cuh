@@ -119,7 +119,13 @@ struct FieldP {
     int zchunk;
     int nbx, nby, nbz;   // field-block grid (for jdirty)
     int tma_b;           // 1: the TMA-fed B pass takes the blocks field_b_tma_block admits
+    long long wait_polls;  // bounded waits of the TMA-fed passes (kWaitPolls by default)
+    const float *inv_eps;  // 1 / eps_r per cell (Eq. consteps) for the fused update, null: vacuum
 };
+
+// Polls of a bounded mbarrier wait before it gives up (~0.5 s with the
+// back-off); the drain of copies in flight always uses this bound.
+constexpr long long kWaitPolls = 1LL << 23;
 
 constexpr int kFieldBX = 32, kFieldBY = 8;
 
@@ -175,6 +181,24 @@ struct ParticleLaunch {
     int *status;
 };
 
+// Let `func` take as much dynamic shared memory as the device allows (the
+// opt-in limit less its static shared memory).  The limit is a property of
+// the function, shared by every simulation of the process: setting it to one
+// simulation's size would refuse the launches of another with a larger box.
+template <class F>
+inline cudaError_t allow_max_dynamic_smem(F *func) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes a{};
+    e = cudaFuncGetAttributes(&a, func);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)a.sharedSizeBytes);
+}
+
 // TMA descriptors of the field arrays (ping-pong E and B, J)
 struct TmaMaps {
     CUtensorMap E[2][3];
@@ -190,7 +214,10 @@ cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s);
 // inv_eps: 1 / eps_r per cell (Eq. consteps), or null: vacuum
 cudaError_t launch_field_e(const GridP &g, const FieldP &f, const float *inv_eps, cudaStream_t s);
 cudaError_t launch_field_stream(const GridP &g, const FieldP &f, cudaStream_t s);
-cudaError_t launch_japply(const GridP &g, const FieldP &f, long long *counter, cudaStream_t s);
+// E^{n+1} -= (dt / eps0) J (x 1/eps_r where inv_eps is set) over the flagged
+// blocks, J and the flags cleared; counter advanced (the step's particle phase ran)
+cudaError_t launch_japply(const GridP &g, const FieldP &f, const float *inv_eps, long long *counter,
+                          cudaStream_t s);
 cudaError_t launch_batch_field(int dims, const GridP *grids, const FieldP *fdescs, const int *fpar,
                                const int *active, const int4 *items, int nitems, cudaStream_t s);
 bool encode_field_maps(const GridP &g, float *const E[2][3], float *const B[2][3],
@@ -202,11 +229,14 @@ cudaError_t launch_field_b_tma(const GridP &g, const FieldP &f, const TmaMaps &m
 cudaError_t launch_field_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
                              int *status, cudaStream_t s);
 cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, cudaStream_t s);
-// ext: launch the batch kernel with the external field and the anisotropic
-// bound push (some member has either)
+// ext: launch the batch kernel with the boundary variants and the
+// anisotropic bound push (some member has one); shape 2: the TSC batch
+// kernel (the group's members all have TSC shapes); done: the members'
+// device step counts (the diffuse draws' step index)
 cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const int *fpar,
                                   const int *active, const int2 *items, int nitems, int *sched,
-                                  int nctas, size_t smem, bool ext, cudaStream_t s);
+                                  const long long *done, int nctas, size_t smem, bool ext,
+                                  int shape, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
 // ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
 // variants (external field, diffuse reflection)
@@ -235,6 +265,13 @@ int scan_kernel_count(long long n);
 cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP &src,
                                 const uint32_t *pid_src, SpeciesP &dst, uint32_t *pid_dst,
                                 const int *start, const int *rank, bool spread, cudaStream_t s);
+// cell-interleaved order inside each tile, in chunks of `chunk` cells (src
+// tile-grouped -> dst); rank: per-particle scratch
+cudaError_t launch_tile_interleave(const TileP &tp, const SpeciesP &src, const uint32_t *pid_src,
+                                   SpeciesP &dst, uint32_t *pid_dst, const int *start, int *rank,
+                                   int chunk, cudaStream_t s);
+// threads of a particle-kernel CTA (the chunk of the interleaved order)
+constexpr int kParticleThreads = 256;
 long long active_tiles_work_len(long long ntiles);
 int active_tiles_kernel_count(long long ntiles);
 cudaError_t launch_active_tiles_work(const TileP &tp, const int *const *starts_dev, int nsp,

@@ -147,6 +147,35 @@ def random_bound(rng, n, count, mask=None, dscale=1e-12, vscale=1e4):
 # workloads
 # ---------------------------------------------------------------------------
 
+def dirac_sheet_ring(nx, ny, k0, q, dx, vF, ppc_side=4, drift=0.1):
+    """Quiet start of a sheet of Dirac carriers in the node plane z = k0 of
+    an nx x ny x nz grid: a ppc_side x ppc_side lattice per cell (z offset
+    exactly 0, so the sheet stays one node plane thick), in-plane directions
+    evenly spaced over the circle (no net current per cell), each then
+    tilted toward +x by drift * cos(q x) and set back to speed v_F.  The
+    sheet starts with a current ripple ~ (drift / 2) v_F cos(q x), uniform
+    density and v_z = 0.  Returns (cell int32, off float32 (N,3), v float32
+    (N,3), ppc)."""
+    ppc = ppc_side * ppc_side
+    a, b = np.meshgrid(np.arange(ppc_side), np.arange(ppc_side), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    th = 2 * math.pi * (a * ppc_side + b + 0.5) / ppc
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    i, j = i.ravel(), j.ravel()
+    fx = (a + 0.5) / ppc_side
+    fy = (b + 0.5) / ppc_side
+    x = (i[:, None] + fx[None, :]) * dx
+    ux = np.cos(th)[None, :] + drift * np.cos(q * x)
+    uy = np.broadcast_to(np.sin(th)[None, :], ux.shape)
+    nrm = np.hypot(ux, uy)
+    cell = ((k0 * ny + j) * nx + i)[:, None] + np.zeros((1, ppc), np.int64)
+    off = np.stack([np.broadcast_to(fx, ux.shape), np.broadcast_to(fy, ux.shape),
+                    np.zeros(ux.shape)], -1)
+    v = np.stack([vF * ux / nrm, vF * uy / nrm, np.zeros(ux.shape)], -1)
+    return (cell.reshape(-1).astype(np.int32), off.reshape(-1, 3).astype(np.float32),
+            v.reshape(-1, 3).astype(np.float32), ppc)
+
+
 def fermi_velocity(E_F, m=ME):
     return math.sqrt(2 * E_F / m)
 

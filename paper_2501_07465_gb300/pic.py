@@ -64,7 +64,7 @@ class pic_tuning(C.Structure):
     _fields_ = [("tile", C.c_int * 3), ("sort_interval", C.c_int), ("field_zchunk", C.c_int),
                 ("particle_ctas", C.c_int), ("keep_J", C.c_int), ("timing", C.c_int),
                 ("field_plain", C.c_int), ("tile_order", C.c_int), ("no_overlap", C.c_int),
-                ("field_mode", C.c_int)]
+                ("field_mode", C.c_int), ("wait_polls", C.c_int64), ("field_overlap", C.c_int)]
 
 
 class pic_diag(C.Structure):
@@ -310,13 +310,16 @@ def pic_load_species(h, desc: pic_species_desc, cell=None, off=None, v=None, anc
 
 
 def pic_set_tuning(h, tile=(0, 0, 0), sort_interval=0, field_zchunk=0, particle_ctas=0,
-                   keep_J=0, timing=0, field_plain=0, tile_order=0, no_overlap=0, field_mode=0):
+                   keep_J=0, timing=0, field_plain=0, tile_order=0, no_overlap=0, field_mode=0,
+                   wait_polls=0, field_overlap=0):
     t = pic_tuning()
     t.tile = (C.c_int * 3)(*tile)
     t.sort_interval, t.field_zchunk, t.particle_ctas = sort_interval, field_zchunk, particle_ctas
     t.keep_J, t.timing, t.field_plain, t.tile_order = keep_J, timing, field_plain, tile_order
     t.no_overlap = no_overlap
     t.field_mode = field_mode  # 0 keeps the current mode
+    t.wait_polls = wait_polls  # 0: the library's bound
+    t.field_overlap = field_overlap  # 0 keeps the current choice
     _check(load_library().pic_set_tuning(h, C.byref(t)), h)
 
 

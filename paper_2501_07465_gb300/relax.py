@@ -65,8 +65,7 @@ def run(densities=(2e28, 4e28, 6e28), ppcs=(16, 32, 64, 128), t_end_fs=20.0, sam
     over t_end_fs.  Particle tile 2 x 2 x 2 cells: at 16-128 particles per
     cell the default 8 x 8 x 4 tile holds up to 32 k particles depositing
     into one shared current box (6x slower, measured).  shape_order 2: TSC
-    for the electrons; such simulations step one after another (a batch
-    group takes CIC members only).
+    for the electrons (the group then runs the TSC batch kernel).
     Returns a dict: per case beta(t) (eV), A (eV / sqrt(fs)), R^2, and the
     whole job's particle-steps / s."""
     wls = [I.bulk_cube(n, p, T_eV=T_eV) for n in densities for p in ppcs]
@@ -79,10 +78,9 @@ def run(densities=(2e28, 4e28, 6e28), ppcs=(16, 32, 64, 128), t_end_fs=20.0, sam
             hs.append(runner.make_sim(wl, stream, dict(tile=tuple(tile)) if tile else None,
                                       shape_order))
         counts = [int(sum(pic.pic_diagnostics(h)["count"])) for h in hs]
-        if shape_order == 1:
-            g = pic.pic_group_create(len(hs), 0, stream, use_graph)
-            for h in hs:
-                pic.pic_group_add(g, h, nsteps)
+        g = pic.pic_group_create(len(hs), 0, stream, use_graph)
+        for h in hs:
+            pic.pic_group_add(g, h, nsteps)
         EF = [wl["species"][0]["E_F"] for wl in wls]
         emax = [3.0 * e for e in EF]
         e_lo = [e + 2 * T_eV * EV for e in EF]
@@ -94,14 +92,8 @@ def run(densities=(2e28, 4e28, 6e28), ppcs=(16, 32, 64, 128), t_end_fs=20.0, sam
         while done < nsteps:
             n = min(chunk, nsteps - done)
             t0 = time.perf_counter()
-            if g is not None:
-                pic.pic_group_step(g, n)
-                pic.pic_group_sync(g)
-            else:
-                for h in hs:
-                    pic.pic_step(h, n)
-                for h in hs:
-                    pic.pic_sync(h)
+            pic.pic_group_step(g, n)
+            pic.pic_group_sync(g)
             wall += time.perf_counter() - t0
             done += n
             t_fs.append(done * dt * 1e15)

@@ -251,6 +251,51 @@ def serve_serial(jobs, tuning=None, result_fn=diagnostics_result, clock=time.per
     return done, _summary(jobs, done, min(j["arrival"] for j in jobs), t_last, "serial")
 
 
+def serial_service_times(jobs, tuning=None, clock=time.perf_counter, sample_steps=None):
+    """Each job run alone through pic_step, back to back, in arrival order:
+    its service time (create, load, steps, diagnostics, destroy).  With
+    sample_steps, a job longer than that runs sample_steps steps and its
+    steps' time is scaled to its full step count (a step of one simulation
+    costs the same all through its run; the sample spans whole re-sort
+    intervals); the create, load, diagnostics and destroy are measured as
+    they are."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = {}
+    for wl in sorted(jobs, key=lambda j: j["arrival"]):
+        t0 = clock()
+        h = runner.make_sim(wl, st.cuda_stream, (tuning or {}).get(wl["grid"]["dims"]))
+        try:
+            pic.pic_sync(h)
+            t1 = clock()
+            n = wl["steps"] if not sample_steps else min(wl["steps"], sample_steps)
+            pic.pic_step(h, n)
+            pic.pic_sync(h)
+            t2 = clock()
+            diagnostics_result(h, wl)
+        finally:
+            pic.pic_destroy(h)
+        t3 = clock()
+        out[wl["job"]] = (t1 - t0) + (t2 - t1) * wl["steps"] / max(n, 1) + (t3 - t2)
+    return out
+
+
+def serial_queue(jobs, service):
+    """One server, first come first served: job j starts when it has arrived
+    and the previous job has finished, and takes its measured service time.
+    The same summary as serve_serial, without running the jobs again (the
+    service time of a job run alone does not depend on when it arrives)."""
+    done = {}
+    free_at = 0.0
+    for wl in sorted(jobs, key=lambda j: j["arrival"]):
+        start = max(wl["arrival"], free_at)
+        free_at = start + service[wl["job"]]
+        done[wl["job"]] = {"latency": free_at - wl["arrival"], "finish": free_at}
+    t_last = max(r["finish"] for r in done.values())
+    return done, _summary(jobs, done, min(j["arrival"] for j in jobs), t_last,
+                          "serial (measured service times, FIFO)")
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--jobs", type=int, default=40)

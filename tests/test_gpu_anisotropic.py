@@ -262,3 +262,38 @@ def test_binding_tensor_arguments():
         assert e.value.status == pic.PIC_EDTLIMIT
     finally:
         pic.pic_destroy(h)
+
+
+def test_binding_tensor_counts_in_later_species_dt_limit():
+    """Eq. dtlimit for a species loaded after a binding tensor uses the
+    tensor's bound, not the diagonal omega0^2 alone.  dx = 1 nm, dt = 1e-18 s:
+    the limit holds while omega_b^2 + omega_p^2 < 2.92e36 s^-2.  The bound
+    species (omega0 = 1e18 s^-1) with off-diagonal entries 0.5 omega0^2 has
+    the Gershgorin bound 2e36 (accepted); a free species adding
+    omega_p^2 = 1.2e36 then exceeds the limit (it would pass against the
+    diagonal 1e36)."""
+    pic = _pic()
+    n = (8, 8, 8)
+    grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
+    rng = np.random.default_rng(8)
+    cb, anc, disp, vb = I.random_bound(rng, n, 50)
+    cell, off, v = I.random_particles(rng, n, 50)
+    w0 = 1e18
+    dens = 1.2e36 * I.ME * I.EPS0 / I.QE ** 2
+    for with_tensor in (False, True):
+        h = PR.gpu_sim(grid, None, [])
+        try:
+            pic.pic_load_species(h, pic.species_desc(I.BOUND, -I.QE, I.ME, 1.0,
+                                                     omega0=(w0,) * 3),
+                                 cell=cb, v=vb, anchor_off=anc, disp=disp, density=1.0)
+            if with_tensor:
+                pic.pic_set_binding_tensor(h, 0, [0.5 * w0 ** 2] * 3)
+                with pytest.raises(pic.PicError) as e:
+                    pic.pic_load_species(h, pic.species_desc(I.FREE, -I.QE, I.ME, 1.0),
+                                         cell=cell, off=off, v=v, density=dens)
+                assert e.value.status == pic.PIC_EDTLIMIT
+            else:
+                pic.pic_load_species(h, pic.species_desc(I.FREE, -I.QE, I.ME, 1.0),
+                                     cell=cell, off=off, v=v, density=dens)
+        finally:
+            pic.pic_destroy(h)

@@ -82,8 +82,9 @@ def test_work_function_field_matches_oracle(dims, bc):
 def test_boundary_variant_arguments():
     """Sizes, NaN / infinite fields, |W| > 1e3 eV, unknown edge rules,
     p outside [0, 1] and open edges with a diffuse share are refused with
-    PIC_EINVAL; an external field round-trips at FP32; a group refuses a
-    simulation with a diffuse share and takes one with an external field."""
+    PIC_EINVAL; an external field round-trips at FP32; a group takes a
+    simulation with an external field or with a diffuse share, whose
+    surface rule then stays fixed while it is a member (PIC_ESTATE)."""
     pic = _pic()
     n = (8, 8, 8)
     grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
@@ -120,8 +121,11 @@ def test_boundary_variant_arguments():
         pic.pic_group_remove(g, h)
         pic.pic_set_external_field(h, None)
         pic.pic_set_particle_bc(h, pic.PIC_EDGE_REFLECT, 0.5, 9)
-        with pytest.raises(pic.PicError):
-            pic.pic_group_add(g, h, 1)
+        pic.pic_group_add(g, h, 1)  # a diffuse member steps in its group
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_set_particle_bc(h, pic.PIC_EDGE_OPEN, 0.0, 0)  # not while in a group
+        assert e.value.status == pic.PIC_ESTATE
+        pic.pic_group_remove(g, h)
         pic.pic_set_particle_bc(h, pic.PIC_EDGE_OPEN, 0.0, 0)
     finally:
         if g is not None:

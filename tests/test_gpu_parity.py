@@ -31,6 +31,13 @@ def _gpu():
     yield
 
 
+def _ov(overlap):
+    """Tuning of the field work beside the particle phase: 0 none, 1 the B
+    pass beside it, 2 both field passes beside it (the current applied after
+    the join; the library's default)."""
+    return dict(no_overlap=0 if overlap else 1, field_overlap=overlap)
+
+
 def _pic():
     from paper_2501_07465_gb300 import pic
     return pic
@@ -56,13 +63,17 @@ def _plane_wave_fields(grid):
     return f
 
 
-@pytest.mark.parametrize("dims,bc,src", [(3, (0, 0, 0), False), (3, (1, 1, 1), True),
-                                         (3, (0, 0, 1), True), (2, (1, 0, 0), True),
-                                         (2, (1, 1, 0), False), (2, (0, 0, 0), True)])
-@pytest.mark.parametrize("nx,plain,overlap,mode", [
-    (45, 0, 0, 2), (44, 0, 0, 2), (64, 0, 0, 2), (44, 0, 1, 2),
-    (45, 0, 0, 1), (44, 0, 0, 1), (44, 1, 0, 1), (64, 0, 0, 1), (44, 0, 1, 1), (45, 0, 1, 1),
-    (45, 0, 0, 3), (64, 0, 0, 3), (44, 0, 1, 3), (70, 0, 0, 3)])
+_FIELD_GRIDS = [(3, (0, 0, 0), False), (3, (1, 1, 1), True), (3, (0, 0, 1), True),
+                (2, (1, 0, 0), True), (2, (1, 1, 0), False), (2, (0, 0, 0), True)]
+# the default split passes on every grid; the fused (1) and one-pass (3)
+# field modes, which the step does not use by default, one case each
+_FIELD_CASES = ([g + r for g in _FIELD_GRIDS
+                 for r in ((45, 0, 0, 2), (44, 0, 0, 2), (64, 0, 0, 2), (44, 0, 1, 2))] +
+                [(3, (1, 1, 1), True, 44, 0, 1, 1), (2, (1, 0, 0), True, 45, 1, 0, 1),
+                 (3, (1, 1, 1), True, 45, 0, 0, 3)])
+
+
+@pytest.mark.parametrize("dims,bc,src,nx,plain,overlap,mode", _FIELD_CASES)
 def test_field_update_matches_oracle(dims, bc, src, nx, plain, overlap, mode):
     """mode 2: the split B / E passes (overlap = 1: B beside the particle
     phase).  mode 1, the fused update: nx = 44 and 64 take the TMA-fed kernel
@@ -125,9 +136,9 @@ def _sphere_case(rng, n=(30, 26, 22), radius=8.0, nfree=6000, nbound=4000, bc=(1
 
 
 @pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((32, 28, 24), 0, 2),
-                                            ((32, 28, 24), 1, 2), ((32, 28, 24), 0, 1),
-                                            ((32, 28, 24), 1, 1), ((30, 26, 22), 0, 3),
-                                            ((32, 28, 24), 1, 3)])
+                                            ((32, 28, 24), 1, 2), ((32, 28, 24), 2, 2),
+                                            ((30, 26, 22), 2, 2), ((32, 28, 24), 1, 1),
+                                            ((30, 26, 22), 0, 3)])
 def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
     rng = np.random.default_rng(11)
     grid, mask, species = _sphere_case(rng, n=n)
@@ -144,7 +155,7 @@ def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
                v=species[0]["v"][keep]), species[1]]
     s.close()
     s = PR.oracle_sim(grid, mask, sp)
-    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1, no_overlap=1 - overlap, field_mode=mode))
+    h = PR.gpu_sim(grid, mask, sp, tuning=dict(keep_J=1, field_mode=mode, **_ov(overlap)))
     try:
         pic.pic_step(h, 1)
         s.step(1)
@@ -179,17 +190,16 @@ def test_sphere_one_step_particles_fields_counts(n, overlap, mode):
 
 
 @pytest.mark.parametrize("n,overlap,mode", [((30, 26, 22), 0, 2), ((36, 26, 22), 0, 2),
-                                            ((36, 26, 22), 1, 2), ((36, 26, 22), 0, 1),
-                                            ((36, 26, 22), 1, 1), ((36, 26, 22), 0, 3),
-                                            ((36, 26, 22), 1, 3)])
+                                            ((36, 26, 22), 1, 2), ((36, 26, 22), 2, 2),
+                                            ((36, 26, 22), 1, 1), ((36, 26, 22), 0, 3)])
 def test_sphere_hundred_steps(n, overlap, mode):
     rng = np.random.default_rng(12)
     grid, mask, species = _sphere_case(rng, n=n, vscale=1.5e6)
     pic = _pic()
     n = grid["n"]
     s = PR.oracle_sim(grid, mask, species)
-    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16, no_overlap=1 - overlap,
-                                                   field_mode=mode))
+    h = PR.gpu_sim(grid, mask, species, tuning=dict(sort_interval=16, field_mode=mode,
+                                                   **_ov(overlap)))
     try:
         pic.pic_step(h, 100)
         s.step(100)
@@ -213,8 +223,7 @@ def test_sphere_hundred_steps(n, overlap, mode):
 
 @pytest.mark.parametrize("tile,overlap,mode", [((32, 32, 1), 0, 2), ((16, 8, 1), 0, 2),
                                                ((7, 5, 1), 0, 2), ((16, 8, 1), 1, 2),
-                                               ((16, 8, 1), 0, 1), ((16, 8, 1), 1, 1),
-                                               ((16, 8, 1), 0, 3), ((16, 8, 1), 1, 3)])
+                                               ((16, 8, 1), 1, 1), ((16, 8, 1), 0, 3)])
 def test_free_2d_periodic(tile, overlap, mode):
     """2D3V periodic plasma, ragged tiles, sorting every 4 steps."""
     rng = np.random.default_rng(21)
@@ -575,6 +584,40 @@ def test_tma_b_pass_interior_blocks(overlap):
         s.close()
 
 
+def test_tma_wait_timeout_is_latched_and_the_device_recovers():
+    """The bounded waits of the TMA-fed B pass: with a limit of one poll the
+    pass gives up on its copies, latches PIC_ETIMEOUT (reported by pic_sync),
+    still waits -- at the full bound -- for the copies it has in flight before
+    each CTA exits, and the handle is destroyed cleanly.  A fresh handle then
+    runs the same grid normally and matches the oracle."""
+    n = (96, 40, 64)
+    d = (1e-9, 0.8e-9, 1.1e-9)
+    dt = 0.45 * min(d) / (I.C_LIGHT * math.sqrt(3))
+    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(1, 1, 1), pml_cells=6)
+    fields = _plane_wave_fields(grid)
+    pic = _pic()
+    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_mode=2, wait_polls=1))
+    try:
+        pic.pic_step(h, 3)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_sync(h)
+        assert e.value.status == pic.PIC_ETIMEOUT
+    finally:
+        pic.pic_destroy(h)
+    h = PR.gpu_sim(grid, None, [], fields=fields, tuning=dict(field_mode=2))
+    s = PR.oracle_sim(grid, None, [], fields=fields)
+    try:
+        pic.pic_step(h, 3)
+        pic.pic_sync(h)
+        s.step(3)
+        got = PR.gpu_fields(h, grid)
+        for c in range(6):
+            assert PR.rel_l2(got[c], s.field(c)) < 1e-5, c
+    finally:
+        pic.pic_destroy(h)
+        s.close()
+
+
 @pytest.mark.parametrize("overlap", [0, 1])
 def test_tma_passes_with_current_3d_periodic(overlap):
     """3D periodic plasma (64 x 24 x 40 cells, free electrons everywhere):
@@ -736,3 +779,35 @@ def test_lorentz_half_space_reflection_spectrum_on_gpu():
     err, band = PR.lorentz_reflection_error(trace, **prm)
     assert band.min() < 0.36 * prm["w0"] and band.max() > 0.64 * prm["w0"]
     assert err < 0.01, err
+
+
+def test_a_smaller_box_created_later_does_not_refuse_a_larger_one():
+    """The particle kernels' shared-memory limit is a property of the kernel,
+    not of one simulation: a simulation with a large staged box (16 x 16 x 8
+    tile) still steps after one with a small box (4 x 4 x 2) was created,
+    and both match what they give alone."""
+    rng = np.random.default_rng(41)
+    n = (24, 20, 16)
+    d = (0.5e-9,) * 3
+    dt = 0.5 * d[0] / (I.C_LIGHT * math.sqrt(3))
+    grid = dict(dims=3, n=n, d=d, dt=dt, bc=(0, 0, 0))
+    cell, off, v = I.random_particles(rng, n, 20000, vscale=2e6)
+    species = [dict(kind=I.FREE, q=-I.QE, m=I.ME, w=1e3, cell=cell, off=off, v=v)]
+    pic = _pic()
+    big = PR.gpu_sim(grid, None, species, tuning=dict(tile=(16, 16, 8)))
+    small = PR.gpu_sim(grid, None, species, tuning=dict(tile=(4, 4, 2)))
+    s = PR.oracle_sim(grid, None, species)
+    try:
+        pic.pic_step(big, 3)
+        pic.pic_step(small, 3)
+        s.step(3)
+        for h in (big, small):
+            pic.pic_sync(h)
+            got = PR.gpu_fields(h, grid)
+            for c in range(6):
+                if np.linalg.norm(s.field(c)) > 0:
+                    assert PR.rel_l2(got[c], s.field(c)) < 1e-4, c
+    finally:
+        pic.pic_destroy(big)
+        pic.pic_destroy(small)
+        s.close()

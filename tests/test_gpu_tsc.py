@@ -155,8 +155,8 @@ def test_tsc_keeps_gauss_law_on_the_device():
 
 def test_shape_order_arguments():
     """Orders other than 1 and 2 are refused (PIC_EINVAL), as is a change
-    after species are loaded (PIC_ESTATE); a group refuses a TSC
-    simulation."""
+    after species are loaded (PIC_ESTATE); a group takes a TSC simulation
+    and then refuses a CIC one (its members share one shape order)."""
     pic = _pic()
     n = (8, 8, 8)
     grid = dict(dims=3, n=n, d=(1e-9,) * 3, dt=1e-18, bc=(0, 0, 0))
@@ -176,9 +176,16 @@ def test_shape_order_arguments():
             pic.pic_set_shape_order(h, 1)
         assert e.value.status == pic.PIC_ESTATE
         g = pic.pic_group_create(4)
-        with pytest.raises(pic.PicError) as e:
-            pic.pic_group_add(g, h, 1)
-        assert e.value.status == pic.PIC_EINVAL
+        pic.pic_group_add(g, h, 1)
+        hc = PR.gpu_sim(grid, None, [])
+        try:
+            pic.pic_load_species(hc, desc, cell=cell, off=off, v=v)
+            with pytest.raises(pic.PicError) as e:
+                pic.pic_group_add(g, hc, 1)
+            assert e.value.status == pic.PIC_EINVAL
+        finally:
+            pic.pic_destroy(hc)
+        pic.pic_group_remove(g, h)
     finally:
         if g is not None:
             pic.pic_group_destroy(g)

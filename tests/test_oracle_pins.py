@@ -849,17 +849,22 @@ def test_langmuir_frequency():
     assert abs(wfit / wbg - 1) < 0.01
 
 
-def sheet_plasmon_closed_form(ns, q, m_pl, Lz):
+def sheet_plasmon_closed_form(ns, q, m_pl, Lz, vF):
     """2D plasmon of a sheet of carriers (density ns, plasmon mass m_pl per
-    carrier, Sec. 5) in vacuum: w^2 = ns e^2 kappa / (2 eps0 m_pl), kappa =
+    carrier, Sec. 5) in vacuum: w^2 = ns e^2 kappa g / (2 eps0 m_pl), kappa =
     sqrt(q^2 - w^2 / c^2) (the field's decay rate off the sheet, equal to q
     without retardation).  On a grid periodic in z with period Lz the sheet's
-    images multiply the field at the sheet by coth(kappa Lz / 2).  Solved by
-    fixed-point iteration."""
+    images multiply the field at the sheet by coth(kappa Lz / 2).  Carriers
+    that all move at v_F in uniformly spread directions answer a wave of
+    phase velocity w / q with the factor g(s) = 2 (1/sqrt(1 - s^2) - 1) / s^2,
+    s = q v_F / w (collisionless response of a ring of velocities; 1 + 3 s^2
+    / 4 for small s).  Solved by fixed-point iteration."""
     w2 = ns * QE ** 2 * q / (2 * EPS0 * m_pl)
     for _ in range(60):
         kap = math.sqrt(q * q - w2 / C ** 2)
-        w2 = ns * QE ** 2 * kap / math.tanh(kap * Lz / 2) / (2 * EPS0 * m_pl)
+        s2 = (q * vF) ** 2 / w2
+        g = 2 * (1 / math.sqrt(1 - s2) - 1) / s2
+        w2 = ns * QE ** 2 * kap / math.tanh(kap * Lz / 2) * g / (2 * EPS0 * m_pl)
     return math.sqrt(w2)
 
 
@@ -903,7 +908,7 @@ def test_sheet_plasmon_frequency(mode):
     pF = EF / vF
     md, mpl = pF / (2 * vF), pF / vF
     q = 2 * math.pi * mode / (nx * dx)
-    w = sheet_plasmon_closed_form(ns, q, mpl, nz * dx)
+    w = sheet_plasmon_closed_form(ns, q, mpl, nz * dx, vF)
     k0 = nz // 2
     X, Vv, ppc = sheet_plasmon_particles(nx, ny, k0, q, dx, vF)
     s = O.OracleSim(dims=3, n=(nx, ny, nz), d=(dx, dx, dx), dt=dt, bc=(0, 0, 0))

@@ -74,3 +74,34 @@ def test_noalloc_counts_reject_grids_above_the_limit():
         assert "at most" in str(e.value)
     finally:
         pic.pic_destroy(h)
+
+
+def test_noalloc_counts_of_a_group_member_wait_for_the_group():
+    """A member of a batch group is advanced on the group's stream, so the
+    counts must wait for the group's steps in flight: called straight after
+    pic_group_step (no synchronisation in between), it gives what
+    pic_cell_counts gives once the group has finished."""
+    import torch
+
+    from paper_2501_07465_gb300 import pic
+    n = (64, 56, 1)
+    hs = [_sim(n, 60000 + 5000 * i, 11 + i) for i in range(2)]
+    gstream = torch.cuda.Stream()  # the group's own stream, not the members'
+    g = pic.pic_group_create(4, 0, gstream.cuda_stream, 0)
+    try:
+        for h in hs:
+            pic.pic_group_add(g, h, 40)
+        shape = I.grid_shape(n)
+        for _ in range(2):
+            pic.pic_group_step(g, 20)
+            got = [pic.pic_cell_counts_noalloc(h, 0, shape) for h in hs]
+            ref = [pic.pic_cell_counts(h, 0, shape) for h in hs]
+            for a, b, h in zip(got, ref, hs):
+                assert np.array_equal(a, b)
+                assert a.sum() == pic.pic_diagnostics(h)["count"][0]
+    finally:
+        for h in hs:
+            pic.pic_group_remove(g, h)
+        pic.pic_group_destroy(g)
+        for h in hs:
+            pic.pic_destroy(h)
