@@ -776,11 +776,11 @@ __device__ inline float u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
 // drawn from Lambert's cosine law about the inward normal -sgn e_ax --
 // cos(theta) = sqrt(u1), azimuth 2 pi u2 from the next axis (x -> y -> z);
 // Dirac carriers: the in-plane law sin(theta) = 2 u1 - 1, v_z = 0.
-template <int KIND>
-__device__ inline void diffuse_velocity(float *v, int ax, int sgn, float u1, float u2) {
+__device__ inline void diffuse_velocity(bool dirac, float *v, int ax, int sgn, float u1,
+                                        float u2) {
     const float speed = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     const float vn = sgn > 0 ? -speed : speed;
-    if (KIND == PIC_DIRAC) {
+    if (dirac) {
         const float st = 2.f * u1 - 1.f;
         const float ct = sqrtf((1.f - st) * (1.f + st));
         const float a = vn * ct, b = speed * st;
@@ -798,11 +798,13 @@ __device__ inline void diffuse_velocity(float *v, int ax, int sgn, float u1, flo
     }
 }
 
-// Free electrons and Dirac carriers (species index si), shape order S.
+// Free electrons and Dirac carriers (species index si, dirac: the species is
+// PIC_DIRAC -- one loop body for both kinds, which differ only in the push,
+// keeps the kernel's code small), shape order S.
 // ACC: a fast no-crossing move's current goes to the register sum acc.
-template <int DIM, int KIND, bool X, int S = 1, bool ACC = false, class Box = BoxAcc>
+template <int DIM, bool X, int S = 1, bool ACC = false, class Box = BoxAcc>
 __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &s, int si,
-                                       long long p, const int *org, const Box &box,
+                                       bool dirac, int p, const int *org, const Box &box,
                                        const GlobalAcc<DIM, X> &glob, CellJ &acc) {
     const GridP &g = P.g;
     const uint32_t pc = s.cell[p];
@@ -821,7 +823,7 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
         else gather<DIM>(glob, gc, f0, E, B);
     }
 
-    if (KIND == PIC_DIRAC) dirac_push(v, E, B, s);
+    if (dirac) dirac_push(v, E, B, s);
     else boris(v, E, B, s.hq);
 
     // drift; at most one cell per axis per step
@@ -852,13 +854,13 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
             if (X && !out1 && P.p_diffuse > 0.f) {
                 const int ncross = (sh[0] != 0) + (sh[1] != 0) + (sh[2] != 0);
                 const int ax = sh[0] ? 0 : sh[1] ? 1 : 2;
-                if (ncross == 1 && !(KIND == PIC_DIRAC && ax == 2)) {
+                if (ncross == 1 && !(dirac && ax == 2)) {
                     uint32_t x[4] = {s.pid[p], P.rng_step, (uint32_t)si, kDiffuseStream};
                     philox4x32_10(x, P.diff_key[0], P.diff_key[1]);
                     diffuse = u24(x[0]) < P.p_diffuse;
                     if (diffuse)
-                        diffuse_velocity<KIND>(v, ax, sh[0] + sh[1] + sh[2], u24(x[1]),
-                                               u24(x[2]));
+                        diffuse_velocity(dirac, v, ax, sh[0] + sh[1] + sh[2], u24(x[1]),
+                                         u24(x[2]));
                 }
             }
             for (int a = 0; a < DIM; ++a) {
@@ -921,7 +923,7 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
 // itself is ~100x the per-step move, so differences of stored values would
 // lose most of its bits.
 template <int DIM, bool X, bool ACC = false, class Box = BoxAcc>
-__device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, long long p,
+__device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, int p,
                                   const int *org, const Box &box,
                                   const GlobalAcc<DIM, X> &glob, CellJ &acc) {
     const GridP &g = P.g;
@@ -1035,24 +1037,6 @@ struct BoxWalk {
     }
 };
 
-// Hint that particle p of species s will be read soon: its SoA words are
-// pulled into L2 while the thread works on the particle before it.
-template <int KIND>
-__device__ inline void prefetch_particle(const SpeciesP &s, long long p) {
-    auto pf = [](const void *q) { asm volatile("prefetch.global.L2 [%0];" ::"l"(q)); };
-    pf(s.cell + p);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        pf(s.v[a] + p);
-        if (KIND == PIC_BOUND) {
-            pf(s.anchor32[a] + p);
-            pf(s.disp[a] + p);
-        } else {
-            pf(s.o[a] + p);
-        }
-    }
-}
-
 // One tile of one simulation: stage the field box, push every particle of
 // the tile (all species), flush the J box.  P must live in parameter or shared
 // memory (not global), so that the compiler keeps its fields in registers
@@ -1155,25 +1139,16 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
     acc.e = -1;
     for (int si = 0; si < P.nsp; ++si) {
         const SpeciesP &s = P.sp[si];
-        const long long a = s.tile_start[t], b = s.tile_start[t + 1];
+        // particle indices of a simulation fit int32 (tile_start is int)
+        const int a = s.tile_start[t], b = s.tile_start[t + 1];
         unsigned r = 0;
-        // ACC kernels hint the thread's next particle into L2
-        const long long nb = ACC ? (long long)blockDim.x : 0;
         if (s.kind == PIC_BOUND) {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
-                if (ACC && p + nb < b) prefetch_particle<PIC_BOUND>(s, p + nb);
+            for (int p = a + threadIdx.x; p < b; p += blockDim.x)
                 push_bound<DIM, X, ACC>(P, s, p, org, box, glob, acc);
-            }
-        } else if (s.kind == PIC_DIRAC) {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
-                if (ACC && p + nb < b) prefetch_particle<PIC_DIRAC>(s, p + nb);
-                r += push_mobile<DIM, PIC_DIRAC, X, S, ACC>(P, s, si, p, org, box, glob, acc);
-            }
         } else {
-            for (long long p = a + threadIdx.x; p < b; p += blockDim.x) {
-                if (ACC && p + nb < b) prefetch_particle<PIC_FREE>(s, p + nb);
-                r += push_mobile<DIM, PIC_FREE, X, S, ACC>(P, s, si, p, org, box, glob, acc);
-            }
+            const bool dirac = s.kind == PIC_DIRAC;
+            for (int p = a + threadIdx.x; p < b; p += blockDim.x)
+                r += push_mobile<DIM, X, S, ACC>(P, s, si, dirac, p, org, box, glob, acc);
         }
         if (r) atomicAdd(&s_refl[si], r);
     }
@@ -1271,7 +1246,7 @@ __global__ void __launch_bounds__(kThreads, 4) particle_kernel_ext(ParticleLaunc
 // by the step's begin pass) is added here, so a captured epoch draws afresh
 // at every step.
 template <int DIM, bool X = false, int S = 1>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, S == 2 ? 2 : 3)
     batch_particle_kernel(const ParticleLaunch *descs, const int *fpar, const int *active,
                           const int2 *items, int nitems, int *sched, const long long *done) {
     extern __shared__ float smem[];

@@ -159,15 +159,13 @@ __device__ inline int local_cell_index(const TileP &tp, int t, uint32_t c) {
     return (lz * tp.T[1] + ly) * tp.T[0] + lx;
 }
 
-// exclusive scan over the ncl cells of (count > r), or of the counts
-// themselves for r < 0, each thread owning a run of consecutive cells;
-// out[ncl] = the total (scratch: 32 ints)
-__device__ inline void block_scan_cells(const int *cnt, int r, int ncl, int *out, int *wsum) {
+// exclusive scan of the counts over the ncl cells, each thread owning a run
+// of consecutive cells; out[ncl] = the total (scratch: 32 ints)
+__device__ inline void block_scan_counts(const int *cnt, int ncl, int *out, int *wsum) {
     const int per = (ncl + blockDim.x - 1) / blockDim.x;
     const int c0 = min(threadIdx.x * per, ncl), c1 = min(c0 + per, ncl);
-    auto val = [&](int c) { return r < 0 ? cnt[c] : (int)(cnt[c] > r); };
     int sum = 0;
-    for (int c = c0; c < c1; ++c) sum += val(c);
+    for (int c = c0; c < c1; ++c) sum += cnt[c];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = sum;
     for (int o = 1; o < 32; o <<= 1) {
@@ -188,12 +186,17 @@ __device__ inline void block_scan_cells(const int *cnt, int r, int ncl, int *out
     int run = (w > 0 ? wsum[w - 1] : 0) + x - sum;
     for (int c = c0; c < c1; ++c) {
         out[c] = run;
-        run += val(c);
+        run += cnt[c];
     }
     if (threadIdx.x == blockDim.x - 1) out[ncl] = wsum[(blockDim.x >> 5) - 1];
-    __syncthreads();  // wsum is reused by the next scan
+    __syncthreads();  // wsum is reused
 }
 
+// One CTA per tile (blockDim = chunk).  The chunks are reordered one after
+// another: thread t stands for cell lo + t of the chunk, and for every rank
+// r a warp ballot of (count > r) gives the cells before it within the warp;
+// the warps' totals give the rest (two barriers per chunk, whatever the
+// largest count).
 __global__ void tile_interleave_kernel(TileP tp, SpeciesP src, const uint32_t *pid_src,
                                        SpeciesP dst, uint32_t *pid_dst, const int *start,
                                        int *rank, int rmax, int chunk) {
@@ -204,61 +207,75 @@ __global__ void tile_interleave_kernel(TileP tp, SpeciesP src, const uint32_t *p
     const int a = start[t], b = start[t + 1];
     if (a == b) return;
     const int ncl = tp.T[0] * tp.T[1] * tp.T[2];
-    const int nch = (ncl + chunk - 1) / chunk;
-    int *cnt = sm;                          // [ncl]
-    int *cs = cnt + ncl;                    // [ncl + 1]: particles in the cells before c
-    int *pre = cs + ncl + 1;                // [nch][rmax + 1]: ranks below r of chunk h
-    int *tab = pre + nch * (rmax + 1);      // [rmax][ncl + 1]: cells before c holding more than r
+    const int nw = blockDim.x >> 5;
+    int *cnt = sm;                      // [ncl]
+    int *cs = cnt + ncl;                // [ncl + 1]: particles in the cells before c
+    int *pre = cs + ncl + 1;            // [rmax + 1]: particles of the ranks below r (chunk)
+    int *wt = pre + rmax + 1;           // [rmax][nw]: cells above rank r, per warp
+    int *tab = wt + rmax * nw;          // [rmax][chunk]: cells before c above rank r (chunk)
     for (int c = threadIdx.x; c < ncl; c += blockDim.x) cnt[c] = 0;
-    if (threadIdx.x == 0) s_R = 0;
     __syncthreads();
     for (int i = a + threadIdx.x; i < b; i += blockDim.x)
         rank[i] = atomicAdd(&cnt[local_cell_index(tp, t, src.cell[i])], 1);
     __syncthreads();
-    for (int c = threadIdx.x; c < ncl; c += blockDim.x) atomicMax(&s_R, cnt[c]);
-    __syncthreads();
-    const int R = s_R;
-    const bool interleave = R <= rmax;
-    block_scan_cells(cnt, -1, ncl, cs, wsum);
-    if (interleave) {
-        for (int r = 0; r < R; ++r)
-            block_scan_cells(cnt, r, ncl, tab + (size_t)r * (ncl + 1), wsum);
-        for (int h = threadIdx.x; h < nch; h += blockDim.x) {
-            const int lo = h * chunk, hi = min(lo + chunk, ncl);
-            int acc = 0;
+    block_scan_counts(cnt, ncl, cs, wsum);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    for (int lo = 0; lo < ncl; lo += chunk) {
+        const int hi = min(lo + chunk, ncl);
+        const int c = lo + threadIdx.x;
+        const int k = c < hi ? cnt[c] : 0;
+        if (threadIdx.x == 0) s_R = 0;
+        __syncthreads();
+        if (k > 0) atomicMax(&s_R, k);
+        __syncthreads();
+        const int R = s_R;
+        const bool inter = R <= rmax;
+        if (inter) {
             for (int r = 0; r < R; ++r) {
-                pre[h * (rmax + 1) + r] = acc;
-                const int *row = tab + (size_t)r * (ncl + 1);
-                acc += row[hi] - row[lo];
+                const unsigned m = __ballot_sync(0xffffffffu, k > r);
+                tab[r * chunk + threadIdx.x] = __popc(m & below);
+                if (lane == 0) wt[r * nw + w] = __popc(m);
             }
         }
         __syncthreads();
-    }
-    for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
-        const uint32_t c = src.cell[i];
-        const int lc = local_cell_index(tp, t, c);
-        const int r = rank[i];
-        long long pos;
-        if (interleave) {
-            const int h = lc / chunk, lo = h * chunk;
-            const int *row = tab + (size_t)r * (ncl + 1);
-            pos = cs[lo] + pre[h * (rmax + 1) + r] + row[lc] - row[lo];
-        } else {
-            pos = cs[lc] + r;
-        }
-        const long long d = a + pos;
-        dst.cell[d] = c;
-        pid_dst[d] = pid_src[i];
-        for (int q = 0; q < 3; ++q) mv(dst.v[q], src.v[q], d, (long long)i);
-        if (src.kind == PIC_BOUND) {
-            for (int q = 0; q < 3; ++q) {
-                mv(const_cast<double *>(dst.anchor[q]), src.anchor[q], d, (long long)i);
-                mv(const_cast<float *>(dst.anchor32[q]), src.anchor32[q], d, (long long)i);
-                mv(dst.disp[q], src.disp[q], d, (long long)i);
+        if (inter) {
+            for (int r = 0; r < R; ++r) {
+                int cross = 0;
+                for (int q = 0; q < w; ++q) cross += wt[r * nw + q];
+                tab[r * chunk + threadIdx.x] += cross;
             }
-        } else {
-            for (int q = 0; q < 3; ++q) mv(dst.o[q], src.o[q], d, (long long)i);
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int r = 0; r < R; ++r) {
+                    pre[r] = acc;
+                    for (int q = 0; q < nw; ++q) acc += wt[r * nw + q];
+                }
+            }
         }
+        __syncthreads();
+        for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+            const uint32_t cell = src.cell[i];
+            const int lc = local_cell_index(tp, t, cell);
+            if (lc < lo || lc >= hi) continue;
+            const int r = rank[i];
+            const long long pos =
+                inter ? cs[lo] + pre[r] + tab[r * chunk + (lc - lo)] : cs[lc] + r;
+            const long long d = a + pos;
+            dst.cell[d] = cell;
+            pid_dst[d] = pid_src[i];
+            for (int q = 0; q < 3; ++q) mv(dst.v[q], src.v[q], d, (long long)i);
+            if (src.kind == PIC_BOUND) {
+                for (int q = 0; q < 3; ++q) {
+                    mv(const_cast<double *>(dst.anchor[q]), src.anchor[q], d, (long long)i);
+                    mv(const_cast<float *>(dst.anchor32[q]), src.anchor32[q], d, (long long)i);
+                    mv(dst.disp[q], src.disp[q], d, (long long)i);
+                }
+            } else {
+                for (int q = 0; q < 3; ++q) mv(dst.o[q], src.o[q], d, (long long)i);
+            }
+        }
+        __syncthreads();  // the tables are rebuilt for the next chunk
     }
 }
 
@@ -393,33 +410,33 @@ cudaError_t launch_tile_scatter(const GridP &g, const TileP &tp, const SpeciesP 
     return cudaGetLastError();
 }
 
-// Shared memory of the interleave kernel: cell counts, their scan, the
-// per-chunk rank offsets and the per-rank scans, for cell counts up to rmax,
-// within 96 KB.
+// Shared memory of the interleave kernel: cell counts, their scan, and one
+// chunk's per-rank tables for cell counts up to rmax, within 48 KB.
 static int interleave_rmax(int ncl, int chunk) {
-    const long long budget = 96 * 1024 / 4;
-    const long long nch = (ncl + chunk - 1) / chunk;
-    const long long r = (budget - 2LL * ncl - 1 - nch) / (ncl + 1 + nch);
+    const long long budget = 48 * 1024 / 4;
+    const long long nw = chunk / 32;
+    const long long r = (budget - 2LL * ncl - 2) / (1 + nw + chunk);
     return (int)std::max<long long>(0, std::min<long long>(r, 255));
 }
 
 static size_t interleave_smem(int ncl, int chunk, int rmax) {
-    const long long nch = (ncl + chunk - 1) / chunk;
-    return (size_t)(2LL * ncl + 1 + nch * (rmax + 1) + (long long)rmax * (ncl + 1)) * sizeof(int);
+    const long long nw = chunk / 32;
+    return (size_t)(2LL * ncl + 2 + (long long)rmax * (1 + nw + chunk)) * sizeof(int);
 }
 
 cudaError_t launch_tile_interleave(const TileP &tp, const SpeciesP &src, const uint32_t *pid_src,
                                    SpeciesP &dst, uint32_t *pid_dst, const int *start, int *rank,
                                    int chunk, cudaStream_t s) {
     if (src.n <= 0) return cudaSuccess;
+    if (chunk % 32 != 0 || chunk > 1024) return cudaErrorInvalidValue;
     const int ncl = tp.T[0] * tp.T[1] * tp.T[2];
     const int rmax = interleave_rmax(ncl, chunk);
     const size_t smem = interleave_smem(ncl, chunk, rmax);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;  // tile too large to reorder
     cudaError_t e = allow_max_dynamic_smem(tile_interleave_kernel);
     if (e != cudaSuccess) return e;
-    tile_interleave_kernel<<<tp.ntiles, 256, smem, s>>>(tp, src, pid_src, dst, pid_dst, start, rank,
-                                                        rmax, chunk);
+    tile_interleave_kernel<<<tp.ntiles, chunk, smem, s>>>(tp, src, pid_src, dst, pid_dst, start,
+                                                          rank, rmax, chunk);
     return cudaGetLastError();
 }
 
