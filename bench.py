@@ -398,8 +398,15 @@ def run_gpu(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     avg = lambda t, k: t[f"{k}_ms"] / max(t[f"{k}_launches"], 1)
+    # the default 3D tile with CIC shapes and the plain surface rule runs the
+    # lean particle kernel (k_particle_lean.cu; its event span also holds the
+    # launch that completes the particles it deferred to the global list)
+    lean = (args.tile or "8,8,4") == "8,8,4" and args.shape_order == 1 and \
+        args.surface in ("specular", "open")
     kernels = {"particle": dict(bytes=pb, ms=avg(tms, "particle"), ms_overlap=avg(tm, "particle"),
-                                src="k_particle.cuh+k_particle.cu", name="particle_kernel")}
+                                src="k_particle.cuh+k_particle_lean.cu" if lean else
+                                "k_particle.cuh+k_particle.cu",
+                                name="particle_kernel_lean" if lean else "particle_kernel")}
     if split:
         kernels["field_e"] = dict(bytes=fb_e, ms=avg(tms, "field"), ms_overlap=avg(tm, "field"),
                                   src="k_field_split.cu", name="field_e_kernel")
@@ -431,7 +438,8 @@ def run_gpu(args):
     if split and args.overlap:
         ph_ms = max(kernels["particle"]["ms_overlap"], kernels["field_b"]["ms_overlap"])
         ph_b = pb + fb_b
-        phase = {"kernels": "particle_kernel + field_b_kernel (beside it)", "bytes": ph_b,
+        phase = {"kernels": kernels["particle"]["name"] + " + field_b_kernel (beside it)",
+                 "bytes": ph_b,
                  "ms": ph_ms, "achieved": ph_b / (ph_ms / 1e3) / 1e9,
                  "frac": ph_b / (ph_ms / 1e3) / 1e9 / peak}
     sb = survey_step_bytes(wl, nfree, nbound, si)

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
 SOURCES = ["pic_api.cu", "pic_group.cu", "k_field.cu", "k_field_tma.cu", "k_field_split.cu", "k_field_stream.cu",
-           "k_particle.cu", "k_particle_ext.cu", "k_particle_tsc.cu", "k_boundary.cu",
+           "k_particle.cu", "k_particle_ext.cu", "k_particle_tsc.cu", "k_particle_lean.cu", "k_boundary.cu",
            "k_sort.cu", "k_fd.cu", "k_diag.cu", "k_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

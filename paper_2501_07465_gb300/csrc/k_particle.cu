@@ -39,6 +39,7 @@ cudaError_t particle_setup_dim(size_t smem, int *ctas_per_sm) {
     if (e != cudaSuccess) return e;
     e = allow_max_dynamic_smem(particle_kernel<DIM>);
     if (e != cudaSuccess) return e;
+    if (DIM == 3 && (e = particle_lean_setup()) != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, particle_kernel<DIM>,
                                                          kThreads, smem);
 }
@@ -78,6 +79,7 @@ cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, c
     if (nctas < 1) nctas = 1;
     if (pl.shape == 2) return launch_particles_tsc(pl, nctas, smem, s);
     if (particle_launch_ext(pl)) return launch_particles_ext(pl, nctas, smem, s);
+    if (particle_lean_fits(pl)) return launch_particles_lean(pl, nctas, nctas, s);
     if (pl.g.dims == 3) particle_kernel<3><<<nctas, kThreads, smem, s>>>(pl);
     else particle_kernel<2><<<nctas, kThreads, smem, s>>>(pl);
     return cudaGetLastError();

@@ -100,13 +100,12 @@ struct GlobalAcc {
         }
     }
     __device__ inline void add(int c, int x, int y, int z, float v) const {
-        long long o = off(x, y, z);
-        if (o < 0) return;  // deposits beyond a wall are dropped
-        atomicAdd(J[c] + o, v);
-        int gx = (int)(o % g->n[0]);
-        int gy = (int)((o / g->n[0]) % g->n[1]);
-        int gz = (int)(o / ((long long)g->n[0] * g->n[1]));
-        int bz = DIM == 3 ? gz / zchunk : 0;
+        const int gx = wrap_or_neg(x, g->n[0], g->per[0]);
+        const int gy = wrap_or_neg(y, g->n[1], g->per[1]);
+        const int gz = DIM == 3 ? wrap_or_neg(z, g->n[2], g->per[2]) : 0;
+        if (gx < 0 || gy < 0 || gz < 0) return;  // deposits beyond a wall are dropped
+        atomicAdd(J[c] + ((long long)gz * g->n[1] + gy) * g->n[0] + gx, v);
+        const int bz = DIM == 3 ? gz / zchunk : 0;
         jdirty[((long long)bz * nby + gy / kFieldBY) * nbx + gx / kFieldBX] = 1;
     }
 };
@@ -491,21 +490,24 @@ __device__ inline void boris(float *v, const float *E, const float *B, float h) 
 // variant kernel when the entries are equal): the closed form
 // v+ = (a^2 w + a (w x b) + (w.b) b) / (a (a^2 + |b|^2)).  Diagonal gamma
 // (variant kernel only): v+ = adj(M) w / det(M), M = diag(a) + [b]x.
+// The kick and the isotropic solve are written with explicitly rounded
+// operations (__fmaf_rn and friends), so that every kernel that inlines them
+// computes the same bits whatever the compiler contracts around them.
 template <bool X>
 __device__ inline void bound_push(float *v, float *D, const float *E, const float *B,
                                   const SpeciesP &s) {
     const float h = s.hq;
-    float k0 = h * E[0] - s.hw0sq[0] * D[0];
-    float k1 = h * E[1] - s.hw0sq[1] * D[1];
-    float k2 = h * E[2] - s.hw0sq[2] * D[2];
+    float k0 = __fmaf_rn(-s.hw0sq[0], D[0], __fmul_rn(h, E[0]));
+    float k1 = __fmaf_rn(-s.hw0sq[1], D[1], __fmul_rn(h, E[1]));
+    float k2 = __fmaf_rn(-s.hw0sq[2], D[2], __fmul_rn(h, E[2]));
     if (X && s.tensor) {
         // off-diagonal entries of the binding tensor (xy, xz, yz) x dt / 2
         k0 -= s.hw0off[0] * D[1] + s.hw0off[1] * D[2];
         k1 -= s.hw0off[0] * D[0] + s.hw0off[2] * D[2];
         k2 -= s.hw0off[1] * D[0] + s.hw0off[2] * D[1];
     }
-    float vm0 = v[0] + k0, vm1 = v[1] + k1, vm2 = v[2] + k2;
-    float b0 = h * B[0], b1 = h * B[1], b2 = h * B[2];
+    const float vm0 = __fadd_rn(v[0], k0), vm1 = __fadd_rn(v[1], k1), vm2 = __fadd_rn(v[2], k2);
+    const float b0 = __fmul_rn(h, B[0]), b1 = __fmul_rn(h, B[1]), b2 = __fmul_rn(h, B[2]);
     if (X && s.aniso) {
         const float a0 = 1.f + s.gdt2v[0], a1 = 1.f + s.gdt2v[1], a2 = 1.f + s.gdt2v[2];
         const float w0 = (1.f - s.gdt2v[0]) * vm0 + (vm1 * b2 - vm2 * b1);
@@ -526,22 +528,25 @@ __device__ inline void bound_push(float *v, float *D, const float *E, const floa
         D[2] += s.dt * v[2];
         return;
     }
-    float a = 1.f + s.gdt2, cc = 1.f - s.gdt2;
-    float w0 = cc * vm0 + (vm1 * b2 - vm2 * b1);
-    float w1 = cc * vm1 + (vm2 * b0 - vm0 * b2);
-    float w2 = cc * vm2 + (vm0 * b1 - vm1 * b0);
-    float wb = w0 * b0 + w1 * b1 + w2 * b2;
-    float bb = b0 * b0 + b1 * b1 + b2 * b2;
-    float inv = 1.0f / (a * (a * a + bb));
-    float p0 = (a * a * w0 + a * (w1 * b2 - w2 * b1) + wb * b0) * inv;
-    float p1 = (a * a * w1 + a * (w2 * b0 - w0 * b2) + wb * b1) * inv;
-    float p2 = (a * a * w2 + a * (w0 * b1 - w1 * b0) + wb * b2) * inv;
-    v[0] = p0 + k0;
-    v[1] = p1 + k1;
-    v[2] = p2 + k2;
-    D[0] += s.dt * v[0];
-    D[1] += s.dt * v[1];
-    D[2] += s.dt * v[2];
+    // u x b component by component: p q - r t, one rounding for p q
+    auto cross = [](float p, float q, float r, float t) { return __fmaf_rn(p, q, -__fmul_rn(r, t)); };
+    const float a = __fadd_rn(1.f, s.gdt2), cc = __fsub_rn(1.f, s.gdt2);
+    const float w0 = __fmaf_rn(cc, vm0, cross(vm1, b2, vm2, b1));
+    const float w1 = __fmaf_rn(cc, vm1, cross(vm2, b0, vm0, b2));
+    const float w2 = __fmaf_rn(cc, vm2, cross(vm0, b1, vm1, b0));
+    const float wb = __fmaf_rn(w2, b2, __fmaf_rn(w1, b1, __fmul_rn(w0, b0)));
+    const float bb = __fmaf_rn(b2, b2, __fmaf_rn(b1, b1, __fmul_rn(b0, b0)));
+    const float a2 = __fmul_rn(a, a);
+    const float inv = __fdiv_rn(1.0f, __fmul_rn(a, __fadd_rn(a2, bb)));
+    const float p0 = __fmul_rn(__fmaf_rn(wb, b0, __fmaf_rn(a, cross(w1, b2, w2, b1), __fmul_rn(a2, w0))), inv);
+    const float p1 = __fmul_rn(__fmaf_rn(wb, b1, __fmaf_rn(a, cross(w2, b0, w0, b2), __fmul_rn(a2, w1))), inv);
+    const float p2 = __fmul_rn(__fmaf_rn(wb, b2, __fmaf_rn(a, cross(w0, b1, w1, b0), __fmul_rn(a2, w2))), inv);
+    v[0] = __fadd_rn(p0, k0);
+    v[1] = __fadd_rn(p1, k1);
+    v[2] = __fadd_rn(p2, k2);
+    D[0] = __fmaf_rn(s.dt, v[0], D[0]);
+    D[1] = __fmaf_rn(s.dt, v[1], D[1]);
+    D[2] = __fmaf_rn(s.dt, v[2], D[2]);
 }
 
 // Dirac carriers (Sec. 5): Boris with the transverse mass, v_z = 0 (sheet in
@@ -727,6 +732,15 @@ __device__ inline void deposit_nocross_acc(const Box &box, const int *c, const f
     }
 }
 
+// the no-crossing deposit into the box: through the register sum (ACC) or
+// straight into the box's accessor
+template <int DIM, bool ACC, class Box>
+__device__ inline void deposit_nocross_box(const Box &box, const int *c, const float *f0,
+                                           const float *dF, const float *jf, float vz, CellJ &acc) {
+    if constexpr (ACC) deposit_nocross_acc<DIM>(box, c, f0, dF, jf, vz, acc);
+    else deposit_nocross<DIM>(box, c, f0, dF, jf, vz);
+}
+
 // ---------------------------------------------------------------------------
 // one particle
 // ---------------------------------------------------------------------------
@@ -802,7 +816,9 @@ __device__ inline void diffuse_velocity(bool dirac, float *v, int ax, int sgn, f
 // PIC_DIRAC -- one loop body for both kinds, which differ only in the push,
 // keeps the kernel's code small), shape order S.
 // ACC: a fast no-crossing move's current goes to the register sum acc.
-template <int DIM, bool X, int S = 1, bool ACC = false, class Box = BoxAcc>
+// GONLY: always the global accessors (the pass over particles deferred out of
+// a tile by the lean kernel, k_particle_lean.cu); the box is not read.
+template <int DIM, bool X, int S = 1, bool ACC = false, class Box = BoxAcc, bool GONLY = false>
 __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &s, int si,
                                        bool dirac, int p, const int *org, const Box &box,
                                        const GlobalAcc<DIM, X> &glob, CellJ &acc) {
@@ -814,7 +830,7 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
     float v[3] = {s.v[0][p], s.v[1][p], s.v[2][p]};
     float f0[3] = {s.o[0][p], s.o[1][p], DIM == 3 ? s.o[2][p] : 0.f};
     float E[3], B[3];
-    const bool fast = in_core<DIM>(P, lc);
+    const bool fast = !GONLY && in_core<DIM>(P, lc);
     if constexpr (S == 2) {
         if (fast) gather_tsc<DIM>(box, lc, f0, E, B);
         else gather_tsc<DIM>(glob, gc, f0, E, B);
@@ -826,15 +842,18 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
     if (dirac) dirac_push(v, E, B, s);
     else boris(v, E, B, s.hq);
 
-    // drift; at most one cell per axis per step
+    // drift; at most one cell per axis per step.  mv: the move in cells
     float f1[3] = {f0[0], f0[1], f0[2]};
+    float mv[3] = {0.f, 0.f, 0.f};
     int sh[3] = {0, 0, 0};
     for (int a = 0; a < DIM; ++a) {
-        float x = f0[a] + s.dtd[a] * v[a];
+        mv[a] = s.dtd[a] * v[a];
+        float x = f0[a] + mv[a];
         if (!(x > -1.f && x < 2.f)) {
             // more than one cell in one step (or NaN): record and stay put
             atomicOr(P.status, kStatusBounds);
             x = f0[a];
+            mv[a] = 0.f;
         }
         if (x >= 1.f) { sh[a] = 1; x -= 1.f; }
         else if (x < 0.f) { sh[a] = -1; x += 1.f; }
@@ -888,10 +907,16 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
             s.cell[p] = pack_cell(nxc[0], nxc[1], nxc[2]);
         }
     } else if (!(sh[0] | sh[1] | sh[2])) {
-        // stays in its cell: f1 - f0 is exact in FP32 (Sterbenz)
-        const float dF[3] = {f1[0] - f0[0], f1[1] - f0[1], DIM == 3 ? f1[2] - f0[2] : 0.f};
-        if (fast && ACC) deposit_nocross_acc<DIM>(box, lc, f0, dF, s.jfac, v[2], acc);
-        else if (fast) deposit_nocross<DIM>(box, lc, f0, dF, s.jfac, v[2]);
+        // ends in its cell.  A move that stayed there takes the move itself,
+        // not the difference of the stored offsets (an FP32 offset near 1 has
+        // an ulp of 6e-8 cell, a few 1e-5 of a typical move of 1e-3 cell);
+        // the offset's rounding leaves a charge-continuity defect of at most
+        // half an ulp of the offset per move.  A move mirrored back into its
+        // cell takes the difference of the offsets.
+        float dF[3];
+        for (int a = 0; a < 3; ++a)
+            dF[a] = a >= DIM ? 0.f : refl ? f1[a] - f0[a] : mv[a];
+        if (fast) deposit_nocross_box<DIM, ACC>(box, lc, f0, dF, s.jfac, v[2], acc);
         else deposit_nocross<DIM>(glob, gc, f0, dF, s.jfac, v[2]);
     } else {
         int c1l[3] = {lc[0] + sh[0], lc[1] + sh[1], lc[2] + sh[2]};
@@ -922,7 +947,7 @@ __device__ inline unsigned push_mobile(const ParticleLaunch &P, const SpeciesP &
 // directly: it is far below an FP32 ulp of the offset, and the displacement D
 // itself is ~100x the per-step move, so differences of stored values would
 // lose most of its bits.
-template <int DIM, bool X, bool ACC = false, class Box = BoxAcc>
+template <int DIM, bool X, bool ACC = false, class Box = BoxAcc, bool GONLY = false>
 __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, int p,
                                   const int *org, const Box &box,
                                   const GlobalAcc<DIM, X> &glob, CellJ &acc) {
@@ -944,7 +969,7 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, in
         f0[a] = clamp_below_one(xa - fl);
     }
     float E[3], B[3];
-    const bool fast = in_core<DIM>(P, c0);
+    const bool fast = !GONLY && in_core<DIM>(P, c0);
     if (fast) gather<DIM>(box, c0, f0, E, B);
     else {
         int gg[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
@@ -966,8 +991,7 @@ __device__ inline void push_bound(const ParticleLaunch &P, const SpeciesP &s, in
         // more than one cell in one step (or NaN): record, deposit nothing
         atomicOr(P.status, kStatusBounds);
     } else if (!(sh[0] | sh[1] | sh[2])) {
-        if (fast && ACC) deposit_nocross_acc<DIM>(box, c0, f0, dF, s.jfac, v[2], acc);
-        else if (fast) deposit_nocross<DIM>(box, c0, f0, dF, s.jfac, v[2]);
+        if (fast) deposit_nocross_box<DIM, ACC>(box, c0, f0, dF, s.jfac, v[2], acc);
         else {
             int g0[3] = {c0[0] + org[0], c0[1] + org[1], c0[2] + org[2]};
             deposit_nocross<DIM>(glob, g0, f0, dF, s.jfac, v[2]);

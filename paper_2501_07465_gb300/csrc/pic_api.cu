@@ -153,8 +153,10 @@ pic_status setup_tiles(pic_sim *s) {
     dfree(s, s->sort_count);
     const long long nt = tp.ntiles;
     // nactive holds the list length, then the particle kernel's tile counter
-    // and finished-CTA count (zero between launches)
-    if (!alloc_zero(s, &s->active, nt + 1) || !alloc_zero(s, &s->nactive, 4) ||
+    // and finished-CTA count, the lean kernel's deferred-list length and the
+    // finished-CTA count of the kernel that completes it (zero between
+    // launches)
+    if (!alloc_zero(s, &s->active, nt + 1) || !alloc_zero(s, &s->nactive, 8) ||
         !alloc_zero(s, &s->tile_work, active_tiles_work_len(nt)) ||
         !alloc_zero(s, &s->sort_count, nt + 1))
         return fail(s, PIC_ENOMEM, "tile buffers");
@@ -349,6 +351,9 @@ ParticleLaunch particle_params(pic_sim *s) {
     P.sched = s->nactive + 1;
     P.step_counter = s->step_counter;
     P.status = s->status;
+    P.defer = s->defer;
+    P.defer_count = s->nactive + 3;
+    P.defer_sched = s->nactive + 4;
     return P;
 }
 
@@ -812,6 +817,18 @@ pic_status pic_load_species(pic_sim *s, const pic_species_desc *d, const pic_par
         }
     }
     if (!ok) return fail(s, PIC_ENOMEM, "species allocation failed");
+    // the lean kernel's deferred list holds each particle at most once a step
+    long long total = 0;
+    for (int i = 0; i <= id; ++i) total += s->sp[i].n;
+    if (total > s->defer_cap) {
+        dfree(s, s->defer);
+        if (!alloc_zero(s, &s->defer, std::max<long long>(total, 1))) {
+            s->defer = nullptr;
+            s->defer_cap = 0;
+            return fail(s, PIC_ENOMEM, "deferred-particle list");
+        }
+        s->defer_cap = total;
+    }
     SpeciesP dst = species_params(s, sp, 0);
     if (loader) {
         FDRequest r{};
@@ -976,7 +993,8 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             CK(s, cudaEventRecord(s->ev_join, s->aux));
             CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
             CK(s, launch_japply(s->g, f, s->inv_eps, s->step_counter, s->stream));
-            s->launches += 2 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) + (f.tma_b ? 1 : 0);
+            s->launches += 1 + particle_launches(P) + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) +
+                           (f.tma_b ? 1 : 0);
         } else if (s->tun.field_mode == 2) {
             // two streaming passes; the B pass reads only E^n, B^{n-1/2} and
             // writes the other ping-pong half, so with overlap it runs beside
@@ -1007,7 +1025,8 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             record(s, 1, false);
             // each pass is one launch, or two (lean and CPML blocks) with CPML,
             // plus the TMA-fed B pass
-            s->launches += 1 + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) + (f.tma_b ? 1 : 0);
+            s->launches += particle_launches(P) + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) +
+                           (f.tma_b ? 1 : 0);
         } else if (!s->tun.no_overlap) {
             // E^n, B^{n-1/2} are only read by both launches and the update
             // writes the other ping-pong half, so the two can run together;
@@ -1027,7 +1046,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             CK(s, cudaEventRecord(s->ev_join, s->aux));
             CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
             CK(s, launch_japply(s->g, f, s->inv_eps, s->step_counter, s->stream));
-            s->launches += 2 + (stream ? fl : 1);
+            s->launches += 1 + particle_launches(P) + (stream ? fl : 1);
         } else {
             record(s, 0, true);
             CK(s, launch_particles(P, particle_ctas_for(s, P), s->psmem, s->stream));
@@ -1037,7 +1056,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             else if (tma) CK(s, launch_field_tma(s->g, f, s->maps, s->fcur, s->status, s->stream));
             else CK(s, launch_field(s->g, f, s->stream));
             record(s, 1, false);
-            s->launches += 1 + (stream ? fl : 1);
+            s->launches += particle_launches(P) + (stream ? fl : 1);
         }
         s->fcur ^= 1;
         s->steps++;

@@ -179,6 +179,13 @@ struct ParticleLaunch {
     int *sched;              // [2]: next list entry to take, CTAs finished (reset by the last)
     long long *step_counter;
     int *status;
+    // lean kernel (k_particle_lean.cu): particles deferred to the global list
+    // as (species, index), capacity the simulation's particle count; its
+    // length; the finished-CTA count of the kernel that completes it.  Null
+    // defer: the lean kernel is not used.
+    int2 *defer;
+    int *defer_count;
+    int *defer_sched;
 };
 
 // Let `func` take as much dynamic shared memory as the device allows (the
@@ -238,6 +245,15 @@ cudaError_t launch_batch_particles(int dims, const ParticleLaunch *descs, const 
                                   const long long *done, int nctas, size_t smem, bool ext,
                                   int shape, cudaStream_t s);
 size_t particle_smem_bytes(const TileP &tp);
+// the lean 3D CIC kernel of the default tile (k_particle_lean.cu): whether a
+// launch can take it, its shared-memory limit, and the launch of it plus the
+// kernel that completes the particles it deferred (two launches)
+bool particle_lean_fits(const ParticleLaunch &pl);
+cudaError_t particle_lean_setup();
+cudaError_t launch_particles_lean(const ParticleLaunch &pl, int nctas, int ndefer_ctas,
+                                  cudaStream_t s);
+// kernels one launch_particles call starts
+inline int particle_launches(const ParticleLaunch &pl) { return particle_lean_fits(pl) ? 2 : 1; }
 // ctas_per_sm: the plain kernel; ctas_per_sm_ext: the one with the boundary
 // variants (external field, diffuse reflection)
 cudaError_t particle_kernel_setup(int dims, size_t smem, int *ctas_per_sm, int *ctas_per_sm_ext,

@@ -79,6 +79,8 @@ struct pic_sim {
     int *tile_work = nullptr;
     int *sort_count = nullptr, *sort_rank = nullptr, *scan_tmp = nullptr;
     long long rank_cap = 0;
+    int2 *defer = nullptr;    // the lean kernel's deferred-particle list
+    long long defer_cap = 0;  // its capacity: the particles of all species
     int **starts_dev = nullptr;
     int particle_ctas = 1;
     int particle_ctas_ext = 1;  // the same for the kernel with the boundary variants

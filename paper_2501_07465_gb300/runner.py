@@ -58,7 +58,8 @@ def estimate_bytes(wl):
     for admission before the handle exists): ping-pong E and B, J, the
     material mask, CPML coefficients and memory terms, and per particle the
     double-buffered SoA state (cell, id, offsets, velocities; bound: FP64 and
-    FP32 anchors and displacements), plus 16 MB of fixed tables."""
+    FP32 anchors and displacements) and its slot in the deferred-particle
+    list, plus 16 MB of fixed tables."""
     g = wl["grid"]
     nc = cells(wl)
     per_cell = 4 * (12 + 3) + 1 + 8 * 2
@@ -72,5 +73,5 @@ def estimate_bytes(wl):
     b = nc * per_cell + slab * 4 * 8
     for sp in wl["species"]:
         np_ = sp["ppc"] * material_cells(wl)
-        b += np_ * (2 * (4 + 4 + 24) + (2 * (24 + 12 + 12) if sp["kind"] == 1 else 0) + 8)
+        b += np_ * (2 * (4 + 4 + 24) + (2 * (24 + 12 + 12) if sp["kind"] == 1 else 0) + 8 + 8)
     return int(b + (16 << 20))
