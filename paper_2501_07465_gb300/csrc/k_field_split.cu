@@ -137,7 +137,7 @@ __device__ inline float cpml_pre(float *psi_out, int q, float old, float b, floa
 }
 
 template <int DIM, bool PML>
-__global__ void __launch_bounds__(BX * BY) field_b_kernel(GridP g, FieldP f) {
+__global__ void __launch_bounds__(BX * BY, PML ? 4 : 5) field_b_kernel(GridP g, FieldP f) {
     if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
     if (!PML && field_b_tma_block(g, f, blockIdx.x, blockIdx.y, blockIdx.z)) return;  // TMA pass
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -266,8 +266,13 @@ __device__ inline float source_value(const FieldP &f) {
 
 // EPS: a permittivity is set (its own instantiation: the vacuum kernel keeps
 // its registers)
+// Register budgets pinned (a change elsewhere in the kernel once moved the
+// vacuum E pass from 64 to 80 registers and one CTA per SM, 0.166 -> 0.181 ms
+// at 256^3): 4 CTAs of 256 threads per SM (64 registers) for the vacuum lean
+// pass, 3 (80) with CPML memory terms or a permittivity; the B pass 5 (48)
+// and 4 (64).
 template <int DIM, bool PML, bool EPS>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, (PML || EPS) ? 3 : 4)
     field_e_kernel(GridP g, FieldP f, const float *inv_eps) {
     if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
     __shared__ float s_src;

@@ -79,7 +79,9 @@ cudaError_t launch_particles(const ParticleLaunch &pl, int nctas, size_t smem, c
     if (nctas < 1) nctas = 1;
     if (pl.shape == 2) return launch_particles_tsc(pl, nctas, smem, s);
     if (particle_launch_ext(pl)) return launch_particles_ext(pl, nctas, smem, s);
-    if (particle_lean_fits(pl)) return launch_particles_lean(pl, nctas, nctas, s);
+    // the completion of the deferred particles: a small grid (its list is
+    // empty on most steps, and then each CTA only reads the length)
+    if (particle_lean_fits(pl)) return launch_particles_lean(pl, nctas, (nctas + 11) / 12, s);
     if (pl.g.dims == 3) particle_kernel<3><<<nctas, kThreads, smem, s>>>(pl);
     else particle_kernel<2><<<nctas, kThreads, smem, s>>>(pl);
     return cudaGetLastError();
