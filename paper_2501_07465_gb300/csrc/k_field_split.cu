@@ -138,13 +138,18 @@ __device__ inline float cpml_pre(float *psi_out, int q, float old, float b, floa
 
 template <int DIM, bool PML>
 __global__ void __launch_bounds__(BX * BY, PML ? 4 : 5) field_b_kernel(GridP g, FieldP f) {
-    if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
-    if (!PML && field_b_tma_block(g, f, blockIdx.x, blockIdx.y, blockIdx.z)) return;  // TMA pass
+    int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (f.blk[0]) {
+        field_list_block(f, PML ? 2 : (f.tma_b ? 1 : 3), bx, by, bz);
+    } else {
+        if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
+        if (!PML && field_b_tma_block(g, f, bx, by, bz)) return;  // the TMA pass's block
+    }
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int i = blockIdx.x * BX + threadIdx.x % BX;
-    const int j = blockIdx.y * BY + threadIdx.x / BX;
+    const int i = bx * BX + threadIdx.x % BX;
+    const int j = by * BY + threadIdx.x / BX;
     if (i >= nx || j >= ny) return;
-    const int k0 = DIM == 3 ? blockIdx.z * f.zchunk : 0;
+    const int k0 = DIM == 3 ? bz * f.zchunk : 0;
     const int k1 = DIM == 3 ? min(k0 + f.zchunk, nz) : 1;
     const long long pl = (long long)nx * ny;
     // neighbour offsets (+x, +y) with the periodic wrap; beyond a wall E = 0
@@ -274,10 +279,12 @@ __device__ inline float source_value(const FieldP &f) {
 template <int DIM, bool PML, bool EPS>
 __global__ void __launch_bounds__(BX * BY, (PML || EPS) ? 3 : 4)
     field_e_kernel(GridP g, FieldP f, const float *inv_eps) {
-    if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
+    int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (f.blk[0]) field_list_block(f, PML ? 2 : 3, bx, by, bz);
+    else if (block_has_pml<DIM>(g, f) != PML) return;  // the other instantiation's block
     __shared__ float s_src;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const long long bflag = ((long long)blockIdx.z * f.nby + blockIdx.y) * f.nbx + blockIdx.x;
+    const long long bflag = ((long long)bz * f.nby + by) * f.nbx + bx;
     // splitJ: the pass runs beside the particle phase and leaves J (and the
     // block flags) to the current pass that follows it
     const bool jdirty = !f.splitJ && f.jdirty[bflag] != 0;
@@ -289,9 +296,9 @@ __global__ void __launch_bounds__(BX * BY, (PML || EPS) ? 3 : 4)
         __syncthreads();
         src = s_src;
     }
-    const int i = blockIdx.x * BX + threadIdx.x % BX;
-    const int j = blockIdx.y * BY + threadIdx.x / BX;
-    const int k0 = DIM == 3 ? blockIdx.z * f.zchunk : 0;
+    const int i = bx * BX + threadIdx.x % BX;
+    const int j = by * BY + threadIdx.x / BX;
+    const int k0 = DIM == 3 ? bz * f.zchunk : 0;
     const int k1 = DIM == 3 ? min(k0 + f.zchunk, nz) : 1;
     if (i < nx && j < ny) {
         const long long pl = (long long)nx * ny;
@@ -388,6 +395,17 @@ __global__ void __launch_bounds__(BX * BY, (PML || EPS) ? 3 : 4)
 }  // namespace
 
 cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s) {
+    if (f.blk[0]) {  // each launch over its compact block list
+        const int nl = f.nblk[f.tma_b ? 1 : 3], np = f.nblk[2];
+        if (g.dims == 3) {
+            if (nl > 0) field_b_kernel<3, false><<<nl, BX * BY, 0, s>>>(g, f);
+            if (np > 0) field_b_kernel<3, true><<<np, BX * BY, 0, s>>>(g, f);
+        } else {
+            if (nl > 0) field_b_kernel<2, false><<<nl, BX * BY, 0, s>>>(g, f);
+            if (np > 0) field_b_kernel<2, true><<<np, BX * BY, 0, s>>>(g, f);
+        }
+        return cudaGetLastError();
+    }
     dim3 grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY,
               g.dims == 3 ? (g.n[2] + f.zchunk - 1) / f.zchunk : 1);
     const bool pml = f.pml[0] || f.pml[1] || f.pml[2];
@@ -402,6 +420,27 @@ cudaError_t launch_field_b(const GridP &g, const FieldP &f, cudaStream_t s) {
 }
 
 cudaError_t launch_field_e(const GridP &g, const FieldP &f, const float *inv_eps, cudaStream_t s) {
+    if (f.blk[0]) {  // each launch over its compact block list
+        const int nl = f.nblk[3], np = f.nblk[2];
+        if (g.dims == 3) {
+            if (inv_eps) {
+                if (nl > 0) field_e_kernel<3, false, true><<<nl, BX * BY, 0, s>>>(g, f, inv_eps);
+                if (np > 0) field_e_kernel<3, true, true><<<np, BX * BY, 0, s>>>(g, f, inv_eps);
+            } else {
+                if (nl > 0) field_e_kernel<3, false, false><<<nl, BX * BY, 0, s>>>(g, f, nullptr);
+                if (np > 0) field_e_kernel<3, true, false><<<np, BX * BY, 0, s>>>(g, f, nullptr);
+            }
+        } else {
+            if (inv_eps) {
+                if (nl > 0) field_e_kernel<2, false, true><<<nl, BX * BY, 0, s>>>(g, f, inv_eps);
+                if (np > 0) field_e_kernel<2, true, true><<<np, BX * BY, 0, s>>>(g, f, inv_eps);
+            } else {
+                if (nl > 0) field_e_kernel<2, false, false><<<nl, BX * BY, 0, s>>>(g, f, nullptr);
+                if (np > 0) field_e_kernel<2, true, false><<<np, BX * BY, 0, s>>>(g, f, nullptr);
+            }
+        }
+        return cudaGetLastError();
+    }
     dim3 grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY,
               g.dims == 3 ? (g.n[2] + f.zchunk - 1) / f.zchunk : 1);
     const bool pml = f.pml[0] || f.pml[1] || f.pml[2];

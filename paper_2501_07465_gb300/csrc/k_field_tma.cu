@@ -629,16 +629,18 @@ __device__ inline void mbar_arrive(uint64_t *bar) {
 __global__ void __launch_bounds__(NT) field_b_kernel_tma(GridP g, FieldP f,
                                                          const __grid_constant__ TmaMaps maps,
                                                          int cur_buf, int *status) {
-    if (!field_b_tma_block(g, f, blockIdx.x, blockIdx.y, blockIdx.z)) return;  // CTA-uniform
+    int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (f.blk[0]) field_list_block(f, 0, bx, by, bz);
+    else if (!field_b_tma_block(g, f, bx, by, bz)) return;  // CTA-uniform
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)SBP * BSTAGE);
     uint64_t *empty = full + SBP;
     __shared__ int s_abort;
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
-    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i0 = bx * BX, j0 = by * BY;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int k0 = blockIdx.z * f.zchunk, k1 = min(k0 + f.zchunk, nz);
+    const int k0 = bz * f.zchunk, k1 = min(k0 + f.zchunk, nz);
     const int np = k1 - k0 + 1;  // planes k0 .. k1; the top one for E only
     if (threadIdx.x == 0) {
         for (int s = 0; s < SBP; ++s) {
@@ -737,6 +739,12 @@ size_t field_b_tma_smem_bytes() { return (size_t)SBP * BSTAGE + 2 * SBP * 8 + 12
 cudaError_t launch_field_b_tma(const GridP &g, const FieldP &f, const TmaMaps &maps, int cur_buf,
                                int *status, cudaStream_t s) {
     if (!f.tma_b || g.dims != 3) return cudaSuccess;
+    if (f.blk[0]) {
+        if (f.nblk[0] > 0)
+            field_b_kernel_tma<<<f.nblk[0], NT, field_b_tma_smem_bytes(), s>>>(g, f, maps, cur_buf,
+                                                                               status);
+        return cudaGetLastError();
+    }
     dim3 grid((g.n[0] + BX - 1) / BX, (g.n[1] + BY - 1) / BY, (g.n[2] + f.zchunk - 1) / f.zchunk);
     field_b_kernel_tma<<<grid, NT, field_b_tma_smem_bytes(), s>>>(g, f, maps, cur_buf, status);
     return cudaGetLastError();

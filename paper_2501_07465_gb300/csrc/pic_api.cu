@@ -320,6 +320,10 @@ FieldP field_params(pic_sim *s) {
     f.tma_b = (s->tun.field_mode == 2 && s->use_tma && !s->tun.field_plain && s->g.dims == 3) ? 1 : 0;
     f.wait_polls = s->tun.wait_polls > 0 ? s->tun.wait_polls : kWaitPolls;
     f.inv_eps = s->inv_eps;
+    for (int k = 0; k < 4; ++k) {
+        f.blk[k] = s->blk_lists ? s->blk_lists + s->blk_off[k] : nullptr;
+        f.nblk[k] = s->blk_n[k];
+    }
     return f;
 }
 
@@ -522,6 +526,11 @@ pic_status pic_create(const pic_grid_desc *gd, void *stream, pic_sim **out) {
         field_tma_setup() == cudaSuccess)
         s->use_tma = true;
     cudaGetLastError();
+    if (build_block_lists(s) != PIC_OK) {
+        std::string m = s->err;
+        pic_destroy(s);
+        return fail(nullptr, PIC_ENOMEM, m);
+    }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
         std::string m = cudaGetErrorString(cudaGetLastError());
         pic_destroy(s);
@@ -694,6 +703,40 @@ pic_status pic_set_particle_bc(pic_sim *s, int edges, double p_diffuse, uint64_t
 
 namespace pic {
 
+// The field blocks of each launch of the split passes (FieldP.blk): [0] the
+// TMA-fed B pass's, [1] the other blocks without a CPML slab, [2] those with
+// one, [3] all without one.  They follow the block grid, the CPML slabs and
+// whether the TMA-fed B pass is on, so they are rebuilt with the tuning.
+pic_status build_block_lists(pic_sim *s) {
+    dfree(s, s->blk_lists);
+    s->blk_lists = nullptr;
+    const FieldP f = field_params(s);
+    std::vector<int> lists[4];
+    for (int bz = 0; bz < s->nbz; ++bz)
+        for (int by = 0; by < s->nby; ++by)
+            for (int bx = 0; bx < s->nbx; ++bx) {
+                const int q = (bz * s->nby + by) * s->nbx + bx;
+                if (field_block_pml(s->g, f, bx, by, bz)) {
+                    lists[2].push_back(q);
+                    continue;
+                }
+                lists[3].push_back(q);
+                lists[field_b_tma_block(s->g, f, bx, by, bz) ? 0 : 1].push_back(q);
+            }
+    std::vector<int> all;
+    for (int k = 0; k < 4; ++k) {
+        s->blk_off[k] = (int)all.size();
+        s->blk_n[k] = (int)lists[k].size();
+        all.insert(all.end(), lists[k].begin(), lists[k].end());
+    }
+    if (!(s->blk_lists = (int *)dalloc(s, std::max<size_t>(all.size(), 1) * sizeof(int))))
+        return fail(s, PIC_ENOMEM, "field block lists");
+    CK(s, cudaMemcpyAsync(s->blk_lists, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
 pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     pic_tuning nt = s->tun;
     for (int a = 0; a < 3; ++a)
@@ -721,6 +764,7 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t) {
     s->tun = nt;
     pic_status st = setup_tiles(s);
     if (st != PIC_OK) return st;
+    if ((st = build_block_lists(s)) != PIC_OK) return st;
     if (s->nsp > 0) {
         st = sort_all(s, true);
         if (st != PIC_OK) return st;

@@ -121,6 +121,13 @@ struct FieldP {
     int tma_b;           // 1: the TMA-fed B pass takes the blocks field_b_tma_block admits
     long long wait_polls;  // bounded waits of the TMA-fed passes (kWaitPolls by default)
     const float *inv_eps;  // 1 / eps_r per cell (Eq. consteps) for the fused update, null: vacuum
+    // Compact lists of field blocks (linear index (bz * nby + by) * nbx + bx),
+    // so that each launch of the split passes runs its own blocks only:
+    // [0] the TMA-fed B pass's, [1] the other blocks without a CPML slab,
+    // [2] the blocks with one, [3] all blocks without one.  blk[0] null:
+    // every launch covers the whole block grid and skips the others' blocks.
+    const int *blk[4];
+    int nblk[4];
 };
 
 // Polls of a bounded mbarrier wait before it gives up (~0.5 s with the
@@ -144,6 +151,28 @@ __host__ __device__ inline bool field_b_tma_block(const GridP &g, const FieldP &
                      (f.pml[1] && (j0 < P || j0 + kFieldBY > g.n[1] - P)) ||
                      (f.pml[2] && (k0 < P || k1 > g.n[2] - P));
     return !pml;
+}
+
+// Does field block (bx, by, bz) hold a cell of a CPML slab?
+__host__ __device__ inline bool field_block_pml(const GridP &g, const FieldP &f, int bx, int by,
+                                                int bz) {
+    const int P = f.P;
+    const int i0 = bx * kFieldBX, j0 = by * kFieldBY;
+    bool r = (f.pml[0] && (i0 < P || i0 + kFieldBX > g.n[0] - P)) ||
+             (f.pml[1] && (j0 < P || j0 + kFieldBY > g.n[1] - P));
+    if (g.dims == 3 && f.pml[2]) {
+        const int k0 = bz * f.zchunk, k1 = k0 + f.zchunk < g.n[2] ? k0 + f.zchunk : g.n[2];
+        r = r || k0 < P || k1 > g.n[2] - P;
+    }
+    return r;
+}
+
+// Block (bx, by, bz) of a launch over the compact list `kind`
+__device__ inline void field_list_block(const FieldP &f, int kind, int &bx, int &by, int &bz) {
+    const int q = f.blk[kind][blockIdx.x];
+    bx = q % f.nbx;
+    by = (q / f.nbx) % f.nby;
+    bz = q / (f.nbx * f.nby);
 }
 
 // Particle tiling.

@@ -70,6 +70,8 @@ struct pic_sim {
     std::vector<uint8_t> mask_h;
     uint8_t *jdirty = nullptr;
     int nbx = 1, nby = 1, nbz = 1;
+    int *blk_lists = nullptr;  // the split passes' compact block lists (FieldP.blk)
+    int blk_off[4] = {0, 0, 0, 0}, blk_n[4] = {0, 0, 0, 0};
     double *rho_bg = nullptr, *rho = nullptr;
     long long *step_counter = nullptr;
     int *status = nullptr;
@@ -122,6 +124,7 @@ pic_status apply_tuning(pic_sim *s, const pic_tuning *t);
 void *raw_alloc(size_t bytes, cudaStream_t stream);
 void raw_free(void *p, size_t bytes, cudaStream_t stream);
 pic_status rebuild_active(pic_sim *s);
+pic_status build_block_lists(pic_sim *s);
 
 }  // namespace pic
 
