@@ -613,7 +613,10 @@ def run_graphene_leg(args, pic, I, stream, peak):
     oracle."""
     import torch
     wl = I.graphene3d()
-    h = build_sim(pic, I, wl, stream.cuda_stream, dict(timing=1))
+    # the sheet tile (16 x 8 x 1: twice the sheet cells of the default tile
+    # under a box of about the same size)
+    tile = (16, 8, 1)
+    h = build_sim(pic, I, wl, stream.cuda_stream, dict(timing=1, tile=tile))
     n = sum(pic.pic_diagnostics(h)["count"])
     pic.pic_step(h, 10)
     pic.pic_sync(h)
@@ -631,7 +634,7 @@ def run_graphene_leg(args, pic, I, stream, peak):
     fb, _, _, _ = field_bytes(wl)
     pb = particle_bytes(n, 0, int(wl["mask"].sum()))
     steps = args.graphene_steps
-    out = {"workload": wl["name"], "particles": n, "steps": steps,
+    out = {"workload": wl["name"], "particles": n, "steps": steps, "tile": list(tile),
            "value": n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
            "step_roofline_frac": (fb + pb) * steps / (ms / 1e3) / 1e9 / peak,
            "kernel_ms_per_step": {"particle": tm["particle_ms"] / steps,
@@ -642,9 +645,9 @@ def run_graphene_leg(args, pic, I, stream, peak):
             small = I.graphene3d(nx=64, ny=64, nz=64)
             s = oracle_setup(I, small)
             s.step(1)
-            e = gpu_vs_oracle(pic, I, small, s, stream, 1)
+            e = gpu_vs_oracle(pic, I, small, s, stream, 1, dict(tile=tile))
             Xo, Vo, _, _ = s.species(0)
-            hs = build_sim(pic, I, small, stream.cuda_stream)
+            hs = build_sim(pic, I, small, stream.cuda_stream, dict(tile=tile))
             pic.pic_step(hs, 1)
             rd = pic.pic_read_species(hs, 0, Xo.shape[0])
             pic.pic_destroy(hs)
@@ -807,12 +810,12 @@ def timed_oracle_steps(s, steps):
     return (time.perf_counter() - t0) / steps
 
 
-def gpu_vs_oracle(pic, I, wl, s, stream, steps):
+def gpu_vs_oracle(pic, I, wl, s, stream, steps, tuning=None):
     """Fresh GPU run of the workload (same seeds) for `steps` steps against
     the oracle simulation s advanced by the same steps: per-particle velocity
     error (max over particles of |dv| / max(|v|, 1e3 m/s)), E and B relative
     L2 over the grid."""
-    h = build_sim(pic, I, wl, stream.cuda_stream)
+    h = build_sim(pic, I, wl, stream.cuda_stream, tuning)
     try:
         pic.pic_step(h, steps)
         g = wl["grid"]

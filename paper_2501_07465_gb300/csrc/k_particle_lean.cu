@@ -1,10 +1,11 @@
 // k_particle_lean.cu -- the particle phase of a 3D step with CIC shapes on
-// the default tile of 8 x 8 x 4 cells: the same gather, push, drift and
+// the default tile of 8 x 8 x 4 cells (and on 16 x 8 x 1, for one-cell
+// sheets): the same gather, push, drift and
 // Esirkepov deposit as particle_kernel<3> (k_particle.cu; Sec. 4.1 and
 // Appendix A of the paper), organised around the common case.
 //
-//  * The staged box (13 x 13 x 9 nodes per component) has compile-time
-//    dimensions, so the gather reaches the eight nodes of a component from
+//  * The staged box (13 x 13 x 9 nodes per component for 8 x 8 x 4) has
+//    compile-time dimensions, so the gather reaches the eight nodes of a component from
 //    one base index by constant offsets, and all nine components (E, B^n, J)
 //    from one shared-memory base.
 //  * Each thread loads its next particle before it works on the current one
@@ -32,31 +33,53 @@ namespace pic {
 
 namespace {
 
-constexpr int LT0 = 8, LT1 = 8, LT2 = 4;  // the tile
-constexpr int LH = kHalo;                  // box = local cells [-2, T + 2]
-constexpr int LB0 = LT0 + 2 * LH + 1, LB1 = LT1 + 2 * LH + 1, LB2 = LT2 + 2 * LH + 1;
-constexpr int LB01 = LB0 * LB1, LBN = LB01 * LB2;
+constexpr int LH = kHalo;        // box = local cells [-2, T + 2]
 constexpr int kDeferCap = 256;  // per-tile list of crossing moves
 
+// A tile shape of the lean kernel: T0 x T1 x T2 cells, its box B0 x B1 x B2
+// nodes (BN per component).  Instantiated for the default 3D tile 8 x 8 x 4
+// and for 16 x 8 x 1, the shape of a one-cell sheet (the graphene workload:
+// twice the sheet cells of an 8 x 8 x 4 tile under a box of about the same
+// size).
+template <int A, int B, int C>
+struct LeanTile {
+    static constexpr int T0 = A, T1 = B, T2 = C;
+    static constexpr int B0 = A + 2 * LH + 1, B1 = B + 2 * LH + 1, B2 = C + 2 * LH + 1;
+    static constexpr int B01 = B0 * B1, BN = B01 * B2;
+};
+using TileCube = LeanTile<8, 8, 4>;
+using TileSheet = LeanTile<16, 8, 1>;
+
+// the tile constants of TL under the names the kernel code uses
+#define LEAN_CONSTS(TL)                                                                     \
+    [[maybe_unused]] constexpr int LT0 = TL::T0, LT1 = TL::T1, LT2 = TL::T2;                \
+    [[maybe_unused]] constexpr int LB0 = TL::B0, LB1 = TL::B1, LB2 = TL::B2;                \
+    [[maybe_unused]] constexpr int LB01 = TL::B01, LBN = TL::BN
+
+template <class TL>
 __device__ __forceinline__ int lidx(int x, int y, int z) {
+    LEAN_CONSTS(TL);
     return (z + LH) * LB01 + (y + LH) * LB0 + (x + LH);
 }
 
 // The box with constant strides, for deposit_nocross_acc / cellj_flush.
+template <class TL>
 struct LeanBox {
-    static constexpr int b0 = LB0, b01 = LB01;
+    static constexpr int b0 = TL::B0, b01 = TL::B01;
     struct JRef {
         float *base;
-        __device__ __forceinline__ float *operator[](int c) const { return base + (6 + c) * LBN; }
+        __device__ __forceinline__ float *operator[](int c) const { return base + (6 + c) * TL::BN; }
     };
     JRef J;
-    __device__ __forceinline__ int idx(int x, int y, int z) const { return lidx(x, y, z); }
+    __device__ __forceinline__ int idx(int x, int y, int z) const { return lidx<TL>(x, y, z); }
 };
 
 // Trilinear interpolation over the eight nodes from p (node (0, 0, 0)) with
 // the weights x1, y1, z1 of the upper nodes; the same association as
 // interp() of the generic kernel.
+template <class TL>
 __device__ __forceinline__ float tri(const float *p, float x1, float y1, float z1) {
+    LEAN_CONSTS(TL);
     const float x0 = 1.f - x1, y0 = 1.f - y1, z0 = 1.f - z1;
     const float a0 = y0 * (x0 * p[0] + x1 * p[1]) + y1 * (x0 * p[LB0] + x1 * p[LB0 + 1]);
     const float a1 = y0 * (x0 * p[LB01] + x1 * p[LB01 + 1]) +
@@ -68,9 +91,11 @@ __device__ __forceinline__ float tri(const float *p, float x1, float y1, float z
 // axes take the node l with the weight f of node l + 1; half-staggered ones
 // the node m + 1/2 below the particle, m = l (weight f - 1/2) when f >= 1/2,
 // else m = l - 1 (weight f + 1/2).
+template <class TL>
 __device__ __forceinline__ void lean_gather(const float *sm, const int *lc, const float *f,
                                             float *E, float *B) {
-    const int e = lidx(lc[0], lc[1], lc[2]);
+    LEAN_CONSTS(TL);
+    const int e = lidx<TL>(lc[0], lc[1], lc[2]);
     float wh[3];
     int oh[3];
     const int step[3] = {1, LB0, LB01};
@@ -81,16 +106,18 @@ __device__ __forceinline__ void lean_gather(const float *sm, const int *lc, cons
         wh[a] = up ? u : u + 1.0f;
         oh[a] = up ? 0 : -step[a];
     }
-    E[0] = tri(sm + 0 * LBN + e + oh[0], wh[0], f[1], f[2]);
-    E[1] = tri(sm + 1 * LBN + e + oh[1], f[0], wh[1], f[2]);
-    E[2] = tri(sm + 2 * LBN + e + oh[2], f[0], f[1], wh[2]);
-    B[0] = tri(sm + 3 * LBN + e + oh[1] + oh[2], f[0], wh[1], wh[2]);
-    B[1] = tri(sm + 4 * LBN + e + oh[0] + oh[2], wh[0], f[1], wh[2]);
-    B[2] = tri(sm + 5 * LBN + e + oh[0] + oh[1], wh[0], wh[1], f[2]);
+    E[0] = tri<TL>(sm + 0 * LBN + e + oh[0], wh[0], f[1], f[2]);
+    E[1] = tri<TL>(sm + 1 * LBN + e + oh[1], f[0], wh[1], f[2]);
+    E[2] = tri<TL>(sm + 2 * LBN + e + oh[2], f[0], f[1], wh[2]);
+    B[0] = tri<TL>(sm + 3 * LBN + e + oh[1] + oh[2], f[0], wh[1], wh[2]);
+    B[1] = tri<TL>(sm + 4 * LBN + e + oh[0] + oh[2], wh[0], f[1], wh[2]);
+    B[2] = tri<TL>(sm + 5 * LBN + e + oh[0] + oh[1], wh[0], wh[1], f[2]);
 }
 
 // the core of the box: local cells [-1, T] on every axis (as in_core<3>)
+template <class TL>
 __device__ __forceinline__ bool lean_core(const int *c) {
+    LEAN_CONSTS(TL);
     return c[0] >= -1 && c[0] <= LT0 && c[1] >= -1 && c[1] <= LT1 && c[2] >= -1 && c[2] <= LT2;
 }
 
@@ -113,18 +140,20 @@ __device__ __forceinline__ void load_mob(const SpeciesP &s, int p, MobIn &m) {
     m.v[1] = s.v[1][p];
     m.v[2] = s.v[2][p];
 }
+template <class TL>
 __device__ __forceinline__ int lean_mobile(const ParticleLaunch &P, const SpeciesP &s, bool dirac,
                                            int p, const MobIn &m, const int *org, float *sm,
                                            CellJ &acc) {
+    LEAN_CONSTS(TL);
     const uint32_t pc = m.pc;
     const int gc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
     int lc[3];
     local_cell<3>(P, gc, org, lc);
-    if (!lean_core(lc)) return kDeferGlobal;
+    if (!lean_core<TL>(lc)) return kDeferGlobal;
     float v[3] = {m.v[0], m.v[1], m.v[2]};
     const float f0[3] = {m.o[0], m.o[1], m.o[2]};
     float E[3], B[3];
-    lean_gather(sm, lc, f0, E, B);
+    lean_gather<TL>(sm, lc, f0, E, B);
     if (dirac) dirac_push(v, E, B, s);
     else boris(v, E, B, s.hq);
     float f1[3], dF[3];
@@ -136,7 +165,7 @@ __device__ __forceinline__ int lean_mobile(const ParticleLaunch &P, const Specie
         stay = stay && f1[a] >= 0.f && f1[a] < 1.f;
     }
     if (!stay) return kDeferTile;
-    LeanBox box{{sm}};
+    LeanBox<TL> box{{sm}};
     deposit_nocross_acc<3>(box, lc, f0, dF, s.jfac, v[2], acc);
     s.o[0][p] = f1[0];
     s.o[1][p] = f1[1];
@@ -162,8 +191,10 @@ __device__ __forceinline__ void load_bnd(const SpeciesP &s, int p, BndIn &m) {
         m.v[a] = s.v[a][p];
     }
 }
+template <class TL>
 __device__ __forceinline__ int lean_bound(const ParticleLaunch &P, const SpeciesP &s, int p,
                                           const BndIn &m, const int *org, float *sm, CellJ &acc) {
+    LEAN_CONSTS(TL);
     const GridP &g = P.g;
     const uint32_t pc = m.pc;
     const int gc[3] = {cell_x(pc), cell_y(pc), cell_z(pc)};
@@ -179,10 +210,10 @@ __device__ __forceinline__ int lean_bound(const ParticleLaunch &P, const Species
         c0[a] = lc[a] + (int)fl;
         f0[a] = clamp_below_one(xa - fl);
     }
-    if (!lean_core(c0)) return kDeferGlobal;
+    if (!lean_core<TL>(c0)) return kDeferGlobal;
     float v[3] = {m.v[0], m.v[1], m.v[2]};
     float E[3], B[3];
-    lean_gather(sm, c0, f0, E, B);
+    lean_gather<TL>(sm, c0, f0, E, B);
     bound_push<false>(v, D, E, B, s);
     float dF[3];
     bool stay = true;
@@ -193,7 +224,7 @@ __device__ __forceinline__ int lean_bound(const ParticleLaunch &P, const Species
         stay = stay && x >= 0.f && x < 1.f;
     }
     if (!stay) return kDeferTile;
-    LeanBox box{{sm}};
+    LeanBox<TL> box{{sm}};
     deposit_nocross_acc<3>(box, c0, f0, dF, s.jfac, v[2], acc);
     s.disp[0][p] = D[0];
     s.disp[1][p] = D[1];
@@ -230,7 +261,9 @@ __device__ __forceinline__ long long lean_node(const GridP &g, const int *org, i
 
 // Box element e -> (bx, by, bz) with constant box dims, advanced by the CTA
 // width.
+template <class TL>
 struct LeanWalk {
+    static constexpr int LB0 = TL::B0, LB1 = TL::B1, LB01 = TL::B01;
     int bx, by, bz, e;
     static constexpr int kDz = kThreads / LB01, kDy = (kThreads - kDz * LB01) / LB0,
                          kDx = kThreads - kDz * LB01 - kDy * LB0;
@@ -250,8 +283,10 @@ struct LeanWalk {
     }
 };
 
+template <class TL>
 __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsigned *s_refl,
                           int2 *s_def, int *s_ndef) {
+    LEAN_CONSTS(TL);
     const TileP &tp = P.tp;
     const GridP &g = P.g;
     const float hdt = 0.5f * g.dt;
@@ -268,7 +303,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
     if (threadIdx.x == 0) *s_ndef = 0;
     // stage E^n, B^{n-1/2}; zero J
     {
-        LeanWalk w;
+        LeanWalk<TL> w;
         for (w.start(threadIdx.x); w.e < LBN; w.next()) {
             long long o;
             if (inner) o = base + (long long)(w.bz * plane + w.by * nx + w.bx);
@@ -286,7 +321,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
     __syncthreads();
     // B^n = B^{n-1/2} - (dt/2) curl E^n on every node a gather can reach
     {
-        LeanWalk w;
+        LeanWalk<TL> w;
         for (w.start(threadIdx.x); w.e < LBN; w.next()) {
             const int e = w.e;
             if (w.bx + 1 >= LB0 || w.by + 1 >= LB1 || w.bz + 1 >= LB2) continue;  // never gathered
@@ -319,7 +354,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
             for (; p < b; p += kThreads) {
                 const BndIn cur = nxt;
                 if (p + kThreads < b) load_bnd(s, p + kThreads, nxt);
-                const int r = lean_bound(P, s, p, cur, org, sm, acc);
+                const int r = lean_bound<TL>(P, s, p, cur, org, sm, acc);
                 if (r != kDone) lean_defer(P, r, si, p, s_def, s_ndef);
             }
         } else {
@@ -330,13 +365,13 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
             for (; p < b; p += kThreads) {
                 const MobIn cur = nxt;
                 if (p + kThreads < b) load_mob(s, p + kThreads, nxt);
-                const int r = lean_mobile(P, s, dirac, p, cur, org, sm, acc);
+                const int r = lean_mobile<TL>(P, s, dirac, p, cur, org, sm, acc);
                 if (r != kDone) lean_defer(P, r, si, p, s_def, s_ndef);
             }
         }
     }
     {
-        LeanBox box{{sm}};
+        LeanBox<TL> box{{sm}};
         cellj_flush<3>(box, acc);
     }
     __syncthreads();
@@ -376,7 +411,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
     }
     // flush the J box
     if (inner) {
-        LeanWalk w;
+        LeanWalk<TL> w;
         for (w.start(threadIdx.x); w.e < LBN; w.next()) {
             const int e = w.e;
             const float jx = sm[6 * LBN + e], jy = sm[7 * LBN + e], jz = sm[8 * LBN + e];
@@ -397,7 +432,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
         }
     } else {
         const int lane = threadIdx.x & 31;
-        LeanWalk w;
+        LeanWalk<TL> w;
         w.start(threadIdx.x);
         for (int e0 = 0; e0 < LBN; e0 += kThreads, w.next()) {
             long long blk = -1;
@@ -428,6 +463,7 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
 
 // Resident CTAs per SM the lean kernel's registers are sized for (as the
 // plain kernel's: three beside the B pass).
+template <class TL>
 __global__ void __launch_bounds__(kThreads, 3) particle_kernel_lean(ParticleLaunch P) {
     extern __shared__ float smem[];
     __shared__ unsigned s_refl[kMaxSpecies];
@@ -441,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 3) particle_kernel_lean(ParticleLaun
         __syncthreads();
         const int it = s_next;
         if (it >= nact) break;
-        lean_tile(P, P.active[it], smem, s_refl, s_def, &s_ndef);
+        lean_tile<TL>(P, P.active[it], smem, s_refl, s_def, &s_ndef);
     }
     __syncthreads();
     if (threadIdx.x < P.nsp && s_refl[threadIdx.x])
@@ -494,18 +530,33 @@ __global__ void __launch_bounds__(kThreads) particle_deferred_kernel(ParticleLau
     }
 }
 
-bool particle_lean_fits(const ParticleLaunch &pl) {
-    return pl.g.dims == 3 && pl.shape == 1 && pl.tp.T[0] == LT0 && pl.tp.T[1] == LT1 &&
-           pl.tp.T[2] == LT2 && pl.defer != nullptr && !particle_launch_ext(pl);
+template <class TL>
+bool lean_tile_is(const TileP &tp) {
+    return tp.T[0] == TL::T0 && tp.T[1] == TL::T1 && tp.T[2] == TL::T2;
 }
 
-cudaError_t particle_lean_setup() { return allow_max_dynamic_smem(particle_kernel_lean); }
+bool particle_lean_fits(const ParticleLaunch &pl) {
+    return pl.g.dims == 3 && pl.shape == 1 &&
+           (lean_tile_is<TileCube>(pl.tp) || lean_tile_is<TileSheet>(pl.tp)) &&
+           pl.defer != nullptr && !particle_launch_ext(pl);
+}
+
+cudaError_t particle_lean_setup() {
+    cudaError_t e = allow_max_dynamic_smem(particle_kernel_lean<TileCube>);
+    if (e != cudaSuccess) return e;
+    return allow_max_dynamic_smem(particle_kernel_lean<TileSheet>);
+}
 
 cudaError_t launch_particles_lean(const ParticleLaunch &pl, int nctas, int ndefer_ctas,
                                   cudaStream_t s) {
     if (nctas < 1) nctas = 1;
     if (ndefer_ctas < 1) ndefer_ctas = 1;
-    particle_kernel_lean<<<nctas, kThreads, (size_t)9 * LBN * sizeof(float), s>>>(pl);
+    if (lean_tile_is<TileSheet>(pl.tp))
+        particle_kernel_lean<TileSheet>
+            <<<nctas, kThreads, (size_t)9 * TileSheet::BN * sizeof(float), s>>>(pl);
+    else
+        particle_kernel_lean<TileCube>
+            <<<nctas, kThreads, (size_t)9 * TileCube::BN * sizeof(float), s>>>(pl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     particle_deferred_kernel<<<ndefer_ctas, kThreads, 0, s>>>(pl);
