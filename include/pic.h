@@ -149,7 +149,10 @@ typedef struct pic_particles {
 
 /* Tuning of one simulation (defaults in brackets; 0 keeps the default). */
 typedef struct pic_tuning {
-    int tile[3];        /* particle tile, cells [8,8,4 in 3D; 32,32,1 in 2D] */
+    int tile[3];        /* particle tile, cells [8,8,4 in 3D; 32,32,1 in 2D].  In 3D with
+                           CIC shapes and the plain surface rule, 8,8,4 and 16,8,1 (the
+                           shape for one-cell sheets) run a kernel specialised to the
+                           tile; any other tile runs the general one */
     int sort_interval;  /* steps between tile re-sorts [32] */
     int field_zchunk;   /* z planes per field-kernel CTA [16] */
     int particle_ctas;  /* persistent particle CTAs [SMs x occupancy, one CTA per SM
