@@ -24,6 +24,8 @@
 //    tile since the last re-sort), and the overflow of the shared list, go
 //    to a global list that particle_deferred_kernel completes after this
 //    kernel with global gathers and global atomics.
+//  * The box is staged by asynchronous copies (cp.async), all of a thread's
+//    issued before it waits once.
 //  * Tiles whose box lies inside the grid stage and flush without the
 //    periodic wrap and flag the field blocks under the box as a whole (the
 //    flags mean "J may be non-zero there").
@@ -122,6 +124,18 @@ __device__ __forceinline__ bool lean_core(const int *c) {
 }
 
 enum : int { kDone = 0, kDeferTile = 1, kDeferGlobal = 2 };
+
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid); the
+// staging issues the whole box before it waits once
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 
 // Free electron or Dirac carrier whose move stays in its cell: gather, push,
@@ -312,11 +326,12 @@ __device__ void lean_tile(const ParticleLaunch &P, const int t, float *sm, unsig
             if (!in) o = 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                sm[c * LBN + w.e] = in ? __ldg(P.E[c] + o) : 0.f;
-                sm[(3 + c) * LBN + w.e] = in ? __ldg(P.B[c] + o) : 0.f;
+                cp_async4(&sm[c * LBN + w.e], P.E[c] + o, in);
+                cp_async4(&sm[(3 + c) * LBN + w.e], P.B[c] + o, in);
                 sm[(6 + c) * LBN + w.e] = 0.f;
             }
         }
+        cp_async_wait_all();
     }
     __syncthreads();
     // B^n = B^{n-1/2} - (dt/2) curl E^n on every node a gather can reach
