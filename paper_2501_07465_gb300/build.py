@@ -48,10 +48,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         if force or _stale(o, [s] + headers):
-            cmd = [cc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
+            cmd = [cc, *ARCH, *FLAGS, "-Xptxas", "-v", *extra, "-c", s, "-o", o]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+            # the register / stack report of every kernel, kept beside the
+            # object (tests/test_build_resources.py reads it)
+            with open(os.path.join(BUILD, src.replace(".cu", ".ptxas.txt")), "w") as fh:
+                fh.write(r.stderr)
             if verbose and r.stderr:
                 sys.stderr.write(r.stderr)
         return o

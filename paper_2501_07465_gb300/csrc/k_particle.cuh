@@ -99,12 +99,17 @@ struct GlobalAcc {
             return b - h * (dEy_dx - dEx_dy);
         }
     }
+    // (the flagged block from the wrapped coordinates, not by dividing the
+    // offset: a form that skipped off() made the compiler copy the whole
+    // launch block to local memory in the boundary-variant kernel, 2.5 KB a
+    // thread, and doubled its time)
     __device__ inline void add(int c, int x, int y, int z, float v) const {
+        long long o = off(x, y, z);
+        if (o < 0) return;  // deposits beyond a wall are dropped
+        atomicAdd(J[c] + o, v);
         const int gx = wrap_or_neg(x, g->n[0], g->per[0]);
         const int gy = wrap_or_neg(y, g->n[1], g->per[1]);
         const int gz = DIM == 3 ? wrap_or_neg(z, g->n[2], g->per[2]) : 0;
-        if (gx < 0 || gy < 0 || gz < 0) return;  // deposits beyond a wall are dropped
-        atomicAdd(J[c] + ((long long)gz * g->n[1] + gy) * g->n[0] + gx, v);
         const int bz = DIM == 3 ? gz / zchunk : 0;
         jdirty[((long long)bz * nby + gy / kFieldBY) * nbx + gx / kFieldBX] = 1;
     }
