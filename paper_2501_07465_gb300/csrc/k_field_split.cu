@@ -137,7 +137,7 @@ __device__ inline float cpml_pre(float *psi_out, int q, float old, float b, floa
 }
 
 template <int DIM, bool PML>
-__global__ void __launch_bounds__(BX * BY, PML ? 4 : 5) field_b_kernel(GridP g, FieldP f) {
+__global__ void __launch_bounds__(BX * BY, DIM == 3 ? (PML ? 4 : 5) : 8) field_b_kernel(GridP g, FieldP f) {
     int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
     if (f.blk[0]) {
         field_list_block(f, PML ? 2 : (f.tma_b ? 1 : 3), bx, by, bz);
@@ -275,9 +275,9 @@ __device__ inline float source_value(const FieldP &f) {
 // vacuum E pass from 64 to 80 registers and one CTA per SM, 0.166 -> 0.181 ms
 // at 256^3): 4 CTAs of 256 threads per SM (64 registers) for the vacuum lean
 // pass, 3 (80) with CPML memory terms or a permittivity; the B pass 5 (48)
-// and 4 (64).
+// and 4 (64).  2D: the E pass 8 (32) and 6 (40) with CPML, the B pass 8.
 template <int DIM, bool PML, bool EPS>
-__global__ void __launch_bounds__(BX * BY, (PML || EPS) ? 3 : 4)
+__global__ void __launch_bounds__(BX * BY, DIM == 3 ? ((PML || EPS) ? 3 : 4) : (PML ? 6 : 8))
     field_e_kernel(GridP g, FieldP f, const float *inv_eps) {
     int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
     if (f.blk[0]) field_list_block(f, PML ? 2 : 3, bx, by, bz);
