@@ -18,6 +18,18 @@ __device__ inline float clamp_below_one(float f) {
     return f < 1.0f ? f : 0x1.fffffep-1f;
 }
 
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid); the
+// staging issues the whole box before it waits once
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ inline int wrap_or_neg(int i, int n, int per) {
     if (i >= 0 && i < n) return i;
     if (!per) return -1;
@@ -1111,11 +1123,12 @@ __device__ void tile_pass(const ParticleLaunch &P, const int t, float *smem, uns
             long long o = in ? ((long long)gz * g.n[1] + gy) * g.n[0] + gx : 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                box.F[c][w.e] = in ? __ldg(P.E[c] + o) : 0.f;
-                box.F[3 + c][w.e] = in ? __ldg(P.B[c] + o) : 0.f;
+                cp_async4(&box.F[c][w.e], P.E[c] + o, in);
+                cp_async4(&box.F[3 + c][w.e], P.B[c] + o, in);
                 box.J[c][w.e] = 0.f;
             }
         }
+        cp_async_wait_all();
     }
     __syncthreads();
     // B^n = B^{n-1/2} - (dt/2) curl E^n (plain Yee curl); zero outside

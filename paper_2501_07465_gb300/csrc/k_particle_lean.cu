@@ -125,17 +125,6 @@ __device__ __forceinline__ bool lean_core(const int *c) {
 
 enum : int { kDone = 0, kDeferTile = 1, kDeferGlobal = 2 };
 
-// 4-byte asynchronous copy global -> shared (zero-filled when !valid); the
-// staging issues the whole box before it waits once
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 
 // Free electron or Dirac carrier whose move stays in its cell: gather, push,
