@@ -703,6 +703,17 @@ pic_status pic_set_particle_bc(pic_sim *s, int edges, double p_diffuse, uint64_t
 
 namespace pic {
 
+// Kernels the split passes launch for one step: one per non-empty block
+// list (launch_field_b_tma, launch_field_b, launch_field_e skip empty ones).
+int split_field_launches(const FieldP &f) {
+    if (!f.blk[0]) {
+        const bool pml = f.pml[0] || f.pml[1] || f.pml[2];
+        return (pml ? 4 : 2) + (f.tma_b ? 1 : 0);
+    }
+    return (f.tma_b && f.nblk[0] > 0) + (f.nblk[f.tma_b ? 1 : 3] > 0) + 2 * (f.nblk[2] > 0) +
+           (f.nblk[3] > 0);
+}
+
 // The field blocks of each launch of the split passes (FieldP.blk): [0] the
 // TMA-fed B pass's, [1] the other blocks without a CPML slab, [2] those with
 // one, [3] all without one.  They follow the block grid, the CPML slabs and
@@ -1037,8 +1048,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             CK(s, cudaEventRecord(s->ev_join, s->aux));
             CK(s, cudaStreamWaitEvent(s->stream, s->ev_join, 0));
             CK(s, launch_japply(s->g, f, s->inv_eps, s->step_counter, s->stream));
-            s->launches += 1 + particle_launches(P) + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) +
-                           (f.tma_b ? 1 : 0);
+            s->launches += 1 + particle_launches(P) + split_field_launches(f);
         } else if (s->tun.field_mode == 2) {
             // two streaming passes; the B pass reads only E^n, B^{n-1/2} and
             // writes the other ping-pong half, so with overlap it runs beside
@@ -1067,10 +1077,7 @@ pic_status pic_step(pic_sim *s, int nsteps) {
             record(s, 1, true);
             CK(s, launch_field_e(s->g, f, s->inv_eps, s->stream));
             record(s, 1, false);
-            // each pass is one launch, or two (lean and CPML blocks) with CPML,
-            // plus the TMA-fed B pass
-            s->launches += particle_launches(P) + ((f.pml[0] || f.pml[1] || f.pml[2]) ? 4 : 2) +
-                           (f.tma_b ? 1 : 0);
+            s->launches += particle_launches(P) + split_field_launches(f);
         } else if (!s->tun.no_overlap) {
             // E^n, B^{n-1/2} are only read by both launches and the update
             // writes the other ping-pong half, so the two can run together;

@@ -125,6 +125,7 @@ void *raw_alloc(size_t bytes, cudaStream_t stream);
 void raw_free(void *p, size_t bytes, cudaStream_t stream);
 pic_status rebuild_active(pic_sim *s);
 pic_status build_block_lists(pic_sim *s);
+int split_field_launches(const FieldP &f);
 
 }  // namespace pic
 
